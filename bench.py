@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the base64 codec on a GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over the 1 GiB workload: encode a
+buffer of uniform random bytes (seed 1) and decode the encoding. Steps
+rotate over the three lengths 2^30, 2^30+1, 2^30+2 so every padding case
+("==", "=", none) is timed. Inputs (>= 1 GiB) are larger than the 129 MB L2,
+so no flush is needed between steps.
+
+  value      enc+dec input GB/s: (n + m) bytes per step / device time, all ranks
+  roofline   the dominant kernel's algorithmic bytes (read + write) per launch
+             / its CUDA-event duration, against the measured HBM copy peak
+  e2e        the same metric through b64_encode_host / b64_decode_host on
+             pinned host buffers (host<->device copies inside the timing)
+  cpu_baseline  the CPU oracle on a bounded prefix of the workload, all cores
+
+--impl reference times the CPU oracle itself (the reference arm of this
+build): it has no GPU code; under torchrun only rank 0 runs it.
+--config batched runs the 100,000-message workload: one batched launch per
+direction against one launch per message.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GIB = 1 << 30
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ setup
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1200)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", choices=["large", "batched"], default="large")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--small", action="store_true",
+                   help="192 MiB instead of 1 GiB (profiling captures); not a bench value")
+    return p.parse_args(argv)
+
+
+class Dist:
+    """Rank bookkeeping; torch.distributed only for barrier and max/sum."""
+
+    def __init__(self, backend=None):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+        if self.world > 1:
+            import datetime
+
+            import torch.distributed as dist
+
+            if backend is None:
+                import torch
+
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend=backend, timeout=datetime.timedelta(seconds=600))
+            self.pg = True
+            self.backend = backend
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def reduce(self, x: float, op: str) -> float:
+        if not self.pg:
+            return x
+        import torch
+        import torch.distributed as dist
+
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.uuid = None
+        try:
+            import torch
+
+            self.uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            if self.uuid and not self.uuid.startswith("GPU-"):
+                self.uuid = "GPU-" + self.uuid
+        except Exception:
+            self.uuid = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------- CPU oracle timing
+def oracle_throughput(data: np.ndarray, sample_bytes: int, threads: int):
+    """Encode a prefix of ``sample_bytes`` (multiple of 3) and decode its
+    encoding with the CPU oracle, split in aligned chunks over ``threads``
+    threads. Returns (input GB/s of encode+decode, seconds)."""
+    import oracle
+
+    oracle.build()
+    sample = np.ascontiguousarray(data[:sample_bytes])
+    per = (sample_bytes // threads) // 3 * 3
+    cuts = [i * per for i in range(threads)] + [sample_bytes]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        encs = list(ex.map(lambda i: oracle.encode(sample[cuts[i]:cuts[i + 1]]), range(threads)))
+        decs = list(ex.map(lambda e: oracle.decode(e), encs))
+    dt = time.perf_counter() - t0
+    assert all(d[0] == 0 for d in decs)
+    moved = sample_bytes + sum(e.size for e in encs)
+    return moved / dt / 1e9, dt
+
+
+def traffic_from_profile(kernel_tag: str, src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic_1gib.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != src_hash:
+            return None
+        return float(kv[f"{kernel_tag}_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1704_00605_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------ our codec
+def run_large(args, d: Dist):
+    import torch
+
+    import paper_1704_00605_gb300 as pkg
+    from paper_1704_00605_gb300 import workloads as W
+
+    torch.cuda.set_device(d.local_rank)
+    pkg.build.ensure_built()
+    g = pkg.load()
+    dev = torch.device("cuda", d.local_rank)
+    base = (192 << 20) if args.small else GIB
+    lengths = (base, base + 1, base + 2)
+    data = W.uniform_bytes(base + 2, 1)  # the 1 GiB workload's stream (prefix when --small)
+    src_all = torch.from_numpy(data).to(dev)
+    m_max = g.b64_encoded_len(base + 2)
+    enc = torch.empty(m_max, dtype=torch.uint8, device=dev)
+    dec = torch.empty(g.b64_decoded_cap(m_max), dtype=torch.uint8, device=dev)
+    res = torch.empty(3, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, evs=None):
+        n = lengths[i % 3]
+        if evs is not None:
+            evs[0].record(stream)
+        g.b64_encode(src_all[:n], enc)
+        if evs is not None:
+            evs[1].record(stream)
+        m = g.b64_encoded_len(n)
+        g.b64_decode_async(enc[:m], dec, res)
+        if evs is not None:
+            evs[2].record(stream)
+        return n, m
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    # correctness of the path being timed (full round trip, all three lengths)
+    for i in range(3):
+        n, m = step(i)
+        st, outlen, fb = g.parse_result(res)
+        assert (st, outlen, fb) == (0, n, m), (st, outlen, fb)
+        assert torch.equal(dec[:n], src_all[:n])
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(d.local_rank)
+    d.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    moved_in = 0
+    for i in range(args.steps):
+        n, m = step(i, evs[i])
+        moved_in += n + m
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    clk = clocks.stop()
+    st, outlen, fb = g.parse_result(res)
+    n_last = lengths[(args.steps - 1) % 3]
+    assert (st, outlen) == (0, n_last), (st, outlen)
+
+    total_ms = t_start.elapsed_time(t_end)
+    enc_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    dec_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_ms_max = d.reduce(total_ms, "max")
+    moved_all = d.reduce(float(moved_in), "sum")
+    value = moved_all / (total_ms_max / 1e3) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    alg_enc = [lengths[i % 3] + g.b64_encoded_len(lengths[i % 3]) for i in range(args.steps)]
+    alg_dec = alg_enc  # decode reads m characters and writes n bytes
+    enc_gbs = sum(alg_enc) / (sum(enc_ms) / 1e3) / 1e9
+    dec_gbs = sum(alg_dec) / (sum(dec_ms) / 1e3) / 1e9
+    dominant = "decode" if sum(dec_ms) >= sum(enc_ms) else "encode"
+    dom_gbs = dec_gbs if dominant == "decode" else enc_gbs
+    src_hash = kernel_source_hash()
+    traffic = traffic_from_profile(dominant, src_hash)
+
+    line = {
+        "metric": "enc+dec input GB/s (1 GiB buffer, encode then decode)",
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": d.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic: uniform random bytes, numpy default_rng(1), 2^30+2 bytes",
+        "config": {"workload": ("single large buffer: 1 GiB (+1, +2) encode + decode (config 2)"
+                                if not args.small else "192 MiB profiling case (not a bench value)"),
+                   "lengths": list(lengths), "encoded_chars": g.b64_encoded_len(base),
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{d.world}"},
+        "roofline": {"bound": "hbm", "kernel": f"k_{dominant}_tma", "achieved": round(dom_gbs, 1),
+                     "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy, read+write)",
+                     "unit": "GB/s", "frac": round(dom_gbs / peak, 4), "traffic": traffic},
+        "encode": {"ms_per_launch": round(float(np.mean(enc_ms)), 4),
+                   "input_gbs": round(sum(lengths[i % 3] for i in range(args.steps)) /
+                                      (sum(enc_ms) / 1e3) / 1e9, 1),
+                   "hbm_gbs": round(enc_gbs, 1), "hbm_frac": round(enc_gbs / peak, 4)},
+        "decode": {"ms_per_launch": round(float(np.mean(dec_ms)), 4),
+                   "input_gbs": round(sum(g.b64_encoded_len(lengths[i % 3])
+                                          for i in range(args.steps)) /
+                                      (sum(dec_ms) / 1e3) / 1e9, 1),
+                   "hbm_gbs": round(dec_gbs, 1), "hbm_frac": round(dec_gbs / peak, 4)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+
+    if not args.no_e2e and not args.small:
+        line["e2e"] = run_e2e(g, data, d)
+    if d.rank == 0 and d.world == 1 and not args.no_cpu and not args.small:
+        threads = os.cpu_count() or 1
+        sample = 96 << 20
+        v, dt = oracle_throughput(data, sample, threads)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"first {sample} bytes of the workload: encode, then "
+                                          f"decode of its encoding; {threads} threads over "
+                                          f"3-/4-aligned chunks; {dt:.2f} s wall"}
+    return line
+
+
+def run_e2e(g, data, d: Dist):
+    """Host-buffer round trip through the C ABI (pinned memory)."""
+    import torch
+
+    lengths = (GIB, GIB + 1, GIB + 2)
+    h_src = torch.empty(GIB + 2, dtype=torch.uint8, pin_memory=True)
+    h_src.numpy()[:] = data
+    m_max = g.b64_encoded_len(GIB + 2)
+    h_enc = torch.empty(m_max, dtype=torch.uint8, pin_memory=True)
+    h_dec = torch.empty(g.b64_decoded_cap(m_max), dtype=torch.uint8, pin_memory=True)
+    src_np, enc_np, dec_np = h_src.numpy(), h_enc.numpy(), h_dec.numpy()
+
+    def step(i):
+        n = lengths[i % 3]
+        m = len(g.b64_encode_host(src_np[:n], enc_np))
+        st, outlen, fb, _ = g.b64_decode_host(enc_np[:m], dec_np)
+        assert st == 0 and outlen == n
+        return n, m
+
+    step(0)
+    assert np.array_equal(dec_np[:GIB], data[:GIB])
+    k = 3
+    d.barrier()
+    t0 = time.perf_counter()
+    moved = 0
+    hb = 0
+    for i in range(k):
+        n, m = step(i)
+        moved += n + m
+        hb += n + m
+    dt = time.perf_counter() - t0
+    dt = d.reduce(dt, "max")
+    moved = d.reduce(float(moved), "sum")
+    return {"value": round(moved / dt / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": int(hb // k), "d2h_bytes_per_step": int(hb // k),
+            "steps": k, "api": "b64_encode_host + b64_decode_host (pinned host buffers)"}
+
+
+# ------------------------------------------------------ reference arm
+def run_reference(args, d: Dist):
+    """The CPU oracle as it stands, on the host cores, on bounded samples of
+    the same workload (the reference arm of this build)."""
+    from paper_1704_00605_gb300 import workloads as W
+
+    data = W.uniform_bytes(48 << 20, 1)  # prefix of the workload stream
+    threads = os.cpu_count() or 1
+    sample = 24 << 20
+    for _ in range(args.warmup):
+        oracle_throughput(data, 3 << 20, threads)
+    t0 = time.perf_counter()
+    moved = 0
+    for _ in range(args.steps):
+        oracle_throughput(data, sample, threads)
+        moved += sample + 4 * sample // 3
+    dt = time.perf_counter() - t0
+    v = moved / dt / 1e9
+    return {
+        "impl": "reference",
+        "metric": "enc+dec input GB/s (1 GiB buffer, encode then decode)",
+        "value": round(v, 4), "unit": "GB/s", "n_gpus": d.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic: uniform random bytes, numpy default_rng(1)",
+        "config": {"workload": "single large buffer: 1 GiB (+1, +2) encode + decode (config 2)",
+                   "sample": f"{sample} bytes per step"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{sample}-byte prefix of the 1 GiB workload per step, "
+                                   f"encode + decode, {threads} threads"},
+        "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0  # rank 0 alone runs the CPU reference
+        os.environ["WORLD_SIZE"] = "1"
+        d = Dist()
+        print(json.dumps(run_reference(args, d)), flush=True)
+        return 0
+    d = Dist()
+    if args.config == "batched":
+        from paper_1704_00605_gb300 import batch_bench
+
+        line = batch_bench.run(args, d)
+    else:
+        line = run_large(args, d)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,139 @@
+/*
+ * gb64 - base64 codec for NVIDIA GB300 (sm_103a): the C ABI.
+ *
+ * The operations follow Muła & Lemire, "Faster Base64 Encoding and Decoding
+ * using AVX2 Instructions" (arXiv 1704.00605):
+ *   encode  Algorithm 1 (Section 2): every 3 input bytes become four 6-bit
+ *           values, each mapped to a character of Table 1; a final group of
+ *           1 or 2 bytes gets "==" or "=" padding.
+ *   decode  Algorithm 2 (Section 2): every 4 characters become 3 bytes; a
+ *           character outside Table 1 is reported as an error (Section 2,
+ *           "report an error when characters outside of this set are
+ *           encountered"; Appendix B quotes RFC 4648 on the same rule).
+ *
+ * Conventions shared by every call:
+ *   - Pointers named src/dst/in_off/out_off/status/first_bad/outlen/d_result
+ *     are DEVICE pointers owned by the caller (any cudaMalloc/torch memory
+ *     of the current device), unless the name starts with h_ (host memory).
+ *   - stream is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *     do not say "synchronous" only enqueue work on it.
+ *   - src and dst must not overlap. No output is NUL-terminated.
+ *   - Argument errors are found on the host before anything is enqueued and
+ *     return B64_ERR_ARG; CUDA runtime failures return B64_ERR_CUDA. The text
+ *     of the last error of the calling thread is b64_last_error().
+ *   - Decode status: B64_OK, B64_ERR_INVALID_CHAR (first_bad = index of the
+ *     first character that is outside Table 1 and not an accepted padding
+ *     '='), or B64_ERR_BAD_LENGTH (no invalid character, length not a
+ *     multiple of 4; first_bad = m - m % 4). '=' is accepted only as the last
+ *     character, or the last two, of an input whose length is a multiple of
+ *     4. On B64_OK first_bad = m; on an error outlen = 0 and the contents of
+ *     dst are unspecified. Non-zero trailing bits in the final group are
+ *     accepted and dropped (Appendix A's extra check is not applied).
+ */
+#ifndef GB64_H
+#define GB64_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream handle (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *gb64_stream_t;
+
+typedef enum {
+  B64_OK = 0,
+  B64_ERR_INVALID_CHAR = 1,
+  B64_ERR_BAD_LENGTH = 2,
+  B64_ERR_ARG = -1,
+  B64_ERR_CUDA = -2,
+  B64_ERR_NOMEM = -3,
+  B64_ERR_TIMEOUT = -4
+} b64_status;
+
+/* Device-side result of one decode (written by b64_decode_async). */
+typedef struct {
+  int64_t first_bad; /* as for b64_decode */
+  int64_t outlen;    /* bytes written on B64_OK, else 0 */
+  int32_t status;    /* a b64_status */
+  uint32_t internal; /* used by the library while the decode runs */
+} b64_result;
+
+/* Length of the encoding of n bytes: 4 * ceil(n / 3) (Section 2: three
+ * bytes per four characters, padded). Returns SIZE_MAX if it overflows. */
+size_t b64_encoded_len(size_t n);
+
+/* Bytes a decode of m characters may write: 3 * (m / 4). */
+size_t b64_decoded_cap(size_t m);
+
+/* Encode n bytes at src into b64_encoded_len(n) characters at dst
+ * (Algorithm 1). Asynchronous on stream. Returns the output length, or
+ * SIZE_MAX on an argument or CUDA error (see b64_last_error()). n = 0 is
+ * legal and returns 0 without enqueuing work. Any alignment of src and dst
+ * is accepted; 16-byte aligned pointers take the TMA-pipelined kernel. */
+size_t b64_encode(const uint8_t *src, size_t n, char *dst, gb64_stream_t stream);
+
+/* Decode m characters at src into dst (capacity b64_decoded_cap(m) bytes)
+ * (Algorithm 2, strict). SYNCHRONOUS: waits for stream, then stores the
+ * decoded length in *outlen and the first bad index in *first_bad (host
+ * pointers) and returns a b64_status. */
+int b64_decode(const char *src, size_t m, uint8_t *dst, size_t *outlen, size_t *first_bad,
+               gb64_stream_t stream);
+
+/* Asynchronous decode: as b64_decode, but the result goes to the device
+ * struct *d_result (caller-owned device memory, 8-byte aligned) and nothing
+ * waits. Returns B64_OK when the work was enqueued, else an error code. */
+int b64_decode_async(const char *src, size_t m, uint8_t *dst, b64_result *d_result,
+                     gb64_stream_t stream);
+
+/* Host-buffer forms: h_src and h_dst are HOST pointers (pinned memory gives
+ * the full link bandwidth; pageable memory works but is slower). The input
+ * is copied to the device in chunks, coded by the same kernels, and copied
+ * back, with copies and kernels of different chunks overlapped on internal
+ * streams ordered after `stream`. SYNCHRONOUS. The library keeps device and
+ * pinned staging buffers per calling thread (allocated at first use). */
+size_t b64_encode_host(const uint8_t *h_src, size_t n, char *h_dst, gb64_stream_t stream);
+int b64_decode_host(const char *h_src, size_t m, uint8_t *h_dst, size_t *outlen,
+                    size_t *first_bad, gb64_stream_t stream);
+
+/* Batched forms: nmsg messages packed back to back in src, message j at
+ * [in_off[j], in_off[j+1]) with in_off[0] = 0 (int64, device, nmsg + 1
+ * entries, non-decreasing). The library writes out_off[0..nmsg] (device):
+ * the exclusive prefix of b64_encoded_len (encode) or b64_decoded_cap
+ * (decode) of the messages, and message j's output starts at dst +
+ * out_off[j]. One persistent kernel codes every message: a device prefix sum
+ * over per-message tile counts assigns fixed-size tiles, and per-message
+ * padding and error positions are handled inside the kernel (Section 2's
+ * rules per message). Asynchronous; per-message decode results go to
+ * status[j], first_bad[j] (relative to the message start) and outlen[j].
+ * dst must hold out_off[nmsg] bytes: call b64_batch_out_offsets first when
+ * that total is not known. Temporary device memory is taken from the
+ * stream-ordered allocator on `stream` and returned on it. */
+int b64_batch_out_offsets(int decode, const int64_t *in_off, int64_t nmsg, int64_t *out_off,
+                          gb64_stream_t stream);
+int b64_encode_batch(const uint8_t *src, const int64_t *in_off, int64_t nmsg, char *dst,
+                     int64_t *out_off, gb64_stream_t stream);
+int b64_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg, uint8_t *dst,
+                     int64_t *out_off, int32_t *status, int64_t *first_bad, int64_t *outlen,
+                     gb64_stream_t stream);
+
+/* Human-readable name of a b64_status value (static string). */
+const char *b64_status_str(int status);
+
+/* Text of the last error recorded by a call on the calling thread ("" if
+ * none). The pointer stays valid until the thread's next gb64 call. */
+const char *b64_last_error(void);
+
+/* Reads and clears the device-side fault word of the current device: non-zero
+ * when a pipelined kernel gave up on a bounded wait for its own copies
+ * (B64_ERR_TIMEOUT) since the last query. Synchronizes the device. Returns 0,
+ * B64_ERR_TIMEOUT or B64_ERR_CUDA. */
+int b64_device_fault(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB64_H */

@@ -1,0 +1,56 @@
+// Internal interface of the batched kernels (batch.cu) used by the C ABI,
+// the tuner and the serving loop.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gb64 {
+
+// Shape of a batched launch.
+struct BatchConfig {
+  int threads;        // 128, 256 or 512 threads per CTA
+  int64_t tile;       // input bytes (encode, multiple of 48) or characters
+                      // (decode, multiple of 64) per tile
+  int blocks_per_sm;  // persistent CTAs per SM
+};
+
+struct BatchArgs {
+  int decode = 0;
+  const uint8_t* src = nullptr;
+  const int64_t* in_off = nullptr;
+  int64_t nmsg = 0;
+  uint8_t* dst = nullptr;
+  int64_t* out_off = nullptr;
+  int64_t* tile_off = nullptr;  // scratch: nmsg + 1 entries
+  void* parts = nullptr;        // scratch: block totals of the scan
+  int32_t* status = nullptr;    // decode only
+  int64_t* first_bad = nullptr;
+  int64_t* outlen = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+// Bytes of scratch a batch of nmsg messages needs (tile_off + scan parts).
+size_t batch_scratch_bytes(int64_t nmsg);
+
+// Splits a scratch block of batch_scratch_bytes(nmsg) into the two arrays.
+inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** tile_off, void** parts) {
+  *tile_off = static_cast<int64_t*>(scratch);
+  *parts = static_cast<int64_t*>(scratch) + (nmsg + 1);
+}
+
+// Output offsets (and tile offsets) of a batch; first_bad/outlen (decode)
+// are initialised when non-null.
+cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
+                          int64_t* tile_off, int64_t tile, void* parts, int64_t* first_bad,
+                          int64_t* outlen, cudaStream_t stream);
+
+// Offsets + the persistent tile kernel (+ the decode finish kernel).
+cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);
+
+// Valid shapes and the defaults used when the tuner has no entry.
+bool batch_config_valid(int decode, const BatchConfig& c);
+BatchConfig default_batch_config(int decode);
+
+}  // namespace gb64

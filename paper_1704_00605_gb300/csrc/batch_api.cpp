@@ -1,0 +1,129 @@
+// C ABI of the batched calls: argument checks, stream-ordered scratch, and
+// the launch shape chosen by the tuner for the batch's size bucket.
+#include <algorithm>
+
+#include "batch.h"
+#include "internal.h"
+#include "tuner.h"
+
+namespace gb64 {
+
+bool batch_config_valid(int decode, const BatchConfig& c) {
+  if (c.threads != 128 && c.threads != 256 && c.threads != 512) return false;
+  if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return false;
+  if (c.tile < 64 || c.tile > (1 << 24)) return false;
+  return decode ? (c.tile % 64 == 0) : (c.tile % 48 == 0);
+}
+
+BatchConfig default_batch_config(int decode) {
+  return decode ? BatchConfig{256, 8192, 8} : BatchConfig{256, 6144, 8};
+}
+
+namespace {
+
+int check_offsets_args(const int64_t* in_off, int64_t nmsg, const int64_t* out_off) {
+  if (nmsg < 0) {
+    set_error("nmsg must be >= 0");
+    return B64_ERR_ARG;
+  }
+  if (!in_off || !out_off) {
+    set_error("in_off and out_off must not be null");
+    return B64_ERR_ARG;
+  }
+  if ((reinterpret_cast<uintptr_t>(in_off) | reinterpret_cast<uintptr_t>(out_off)) & 7u) {
+    set_error("offset arrays must be 8-byte aligned");
+    return B64_ERR_ARG;
+  }
+  return B64_OK;
+}
+
+int run_batch(BatchArgs a) {
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(a.nmsg), a.stream);
+  if (e != cudaSuccess) return cuda_status(e, "batch: scratch");
+  batch_scratch_split(scratch, a.nmsg, &a.tile_off, &a.parts);
+  const BatchConfig cfg = tuned_batch_config(a.decode, a.nmsg);
+  e = batch_launch(a, cfg);
+  cudaError_t ef = cudaFreeAsync(scratch, a.stream);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return cuda_status(e, "batch: launch");
+  return B64_OK;
+}
+
+}  // namespace
+}  // namespace gb64
+
+using namespace gb64;
+
+extern "C" {
+
+int b64_batch_out_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
+                          gb64_stream_t stream) {
+  clear_error();
+  int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc != B64_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(nmsg), s);
+  if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets: scratch");
+  int64_t* tile_off;
+  void* parts;
+  batch_scratch_split(scratch, nmsg, &tile_off, &parts);
+  e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, tile_off, 1 << 20, parts, nullptr,
+                    nullptr, s);
+  cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets");
+  return B64_OK;
+}
+
+int b64_encode_batch(const uint8_t* src, const int64_t* in_off, int64_t nmsg, char* dst,
+                     int64_t* out_off, gb64_stream_t stream) {
+  clear_error();
+  int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc != B64_OK) return rc;
+  if (nmsg > 0 && (!src || !dst)) {
+    set_error("src and dst must not be null");
+    return B64_ERR_ARG;
+  }
+  BatchArgs a;
+  a.decode = 0;
+  a.src = src;
+  a.in_off = in_off;
+  a.nmsg = nmsg;
+  a.dst = reinterpret_cast<uint8_t*>(dst);
+  a.out_off = out_off;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  return run_batch(a);
+}
+
+int b64_decode_batch(const char* src, const int64_t* in_off, int64_t nmsg, uint8_t* dst,
+                     int64_t* out_off, int32_t* status, int64_t* first_bad, int64_t* outlen,
+                     gb64_stream_t stream) {
+  clear_error();
+  int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc != B64_OK) return rc;
+  if (nmsg > 0 && (!src || !dst || !status || !first_bad || !outlen)) {
+    set_error("src, dst, status, first_bad and outlen must not be null");
+    return B64_ERR_ARG;
+  }
+  if ((reinterpret_cast<uintptr_t>(first_bad) | reinterpret_cast<uintptr_t>(outlen)) & 7u ||
+      reinterpret_cast<uintptr_t>(status) & 3u) {
+    set_error("result arrays must be naturally aligned");
+    return B64_ERR_ARG;
+  }
+  BatchArgs a;
+  a.decode = 1;
+  a.src = reinterpret_cast<const uint8_t*>(src);
+  a.in_off = in_off;
+  a.nmsg = nmsg;
+  a.dst = dst;
+  a.out_off = out_off;
+  a.status = status;
+  a.first_bad = first_bad;
+  a.outlen = outlen;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  return run_batch(a);
+}
+
+}  // extern "C"

@@ -1,0 +1,354 @@
+// Device building blocks of the gb64 codec (sm_103a).
+//
+// - PTX wrappers for mbarrier and the 1-D TMA bulk copies
+//   (cp.async.bulk global<->shared) with bounded waits.
+// - The alphabet maps: encode maps a 6-bit value to its character by the
+//   five ranges of Table 3 (offsets +65, +71, -4, -19, -16); decode inverts
+//   that map into a 256-entry byte table whose entries outside the alphabet
+//   carry bit 7 (the "invalid" flag, like the zero offset of Section 4.2).
+//   Both live in shared memory; 64 or 256 bytes span at most 32 banks for
+//   every ASCII input, so lookups by a warp never conflict on valid text.
+// - Unit codecs: 12 bytes -> 16 characters (four groups of Algorithm 1's
+//   main loop) and 16 characters -> 12 bytes (four quads of Algorithm 2's
+//   main loop), with bytes regrouped by prmt (__byte_perm) and shifts.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gb64 {
+
+template <typename T>
+__host__ __device__ __forceinline__ T tmin(T a, T b) {
+  return a < b ? a : b;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T tmax(T a, T b) {
+  return a > b ? a : b;
+}
+
+constexpr uint32_t kPadChar = 0x3D;  // '='
+constexpr uint32_t kBadFlag = 0x80;  // decode-table flag for bytes outside the alphabet
+
+// Table 3: 6-bit value -> ASCII code, by range.
+__host__ __device__ constexpr uint32_t alphabet_char(uint32_t v) {
+  return v < 26 ? v + 65 : v < 52 ? v + 71 : v < 62 ? v - 4 : v == 62 ? v - 19 : v - 16;
+}
+
+// Fills the shared tables. enc: 64 bytes; dec: 256 bytes (either may be null).
+__device__ __forceinline__ void init_tables(uint8_t* enc, uint8_t* dec) {
+  if (dec) {
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) dec[i] = (uint8_t)kBadFlag;
+    __syncthreads();
+  }
+  for (uint32_t v = threadIdx.x; v < 64; v += blockDim.x) {
+    const uint32_t c = alphabet_char(v);
+    if (enc) enc[v] = (uint8_t)c;
+    if (dec) dec[c] = (uint8_t)v;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase with the given parity to complete, for at most about
+// limit_ns of wall time. Returns false on timeout (the caller reports it).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && global_timer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` transactions on bar.
+// Both addresses and bytes must be multiples of 16.
+__device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* gsrc, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// 1-D bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void tma_store_1d(void* gdst, const void* smem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"(smem_addr(smem_src)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// All committed bulk stores have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// All committed bulk stores are complete (written to global memory).
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses with later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_global_v4_cs(void* p, uint4 v) {
+  asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+// --------------------------------------------------------------- encode
+// One group of Algorithm 1's main loop. g holds the three bytes big-endian
+// in bits 23..0 (bits above 23 are ignored); returns the four characters as
+// a little-endian word (first character in the low byte).
+__device__ __forceinline__ uint32_t enc_group(uint32_t g, const uint8_t* T) {
+  const uint32_t c0 = T[(g >> 18) & 63u];
+  const uint32_t c1 = T[(g >> 12) & 63u];
+  const uint32_t c2 = T[(g >> 6) & 63u];
+  const uint32_t c3 = T[g & 63u];
+  return __byte_perm(__byte_perm(c0, c1, 0x0040), __byte_perm(c2, c3, 0x0040), 0x5410);
+}
+
+// Four groups: stream bytes x0..x11 in little-endian words w0, w1, w2
+// (x0 = low byte of w0) -> 16 characters.
+__device__ __forceinline__ uint4 enc_unit(uint32_t w0, uint32_t w1, uint32_t w2,
+                                          const uint8_t* T) {
+  uint4 o;
+  o.x = enc_group(__byte_perm(w0, 0u, 0x4012), T);  // x0 x1 x2
+  o.y = enc_group(__byte_perm(w0, w1, 0x3345), T);  // x3 x4 x5
+  o.z = enc_group(__byte_perm(w1, w2, 0x2234), T);  // x6 x7 x8
+  o.w = enc_group(__byte_perm(w2, 0u, 0x4123), T);  // x9 x10 x11
+  return o;
+}
+
+// The last, possibly partial, group: cnt (1..3) bytes b0..b2 -> four
+// characters with "==" (cnt 1) or "=" (cnt 2) padding (Algorithm 1's tail).
+__device__ __forceinline__ uint32_t enc_tail_group(uint32_t b0, uint32_t b1, uint32_t b2,
+                                                   uint32_t cnt, const uint8_t* T) {
+  if (cnt < 2) b1 = 0;
+  if (cnt < 3) b2 = 0;
+  uint32_t w = enc_group((b0 << 16) | (b1 << 8) | b2, T);
+  if (cnt == 1) w = (w & 0x0000FFFFu) | (kPadChar << 16) | (kPadChar << 24);
+  if (cnt == 2) w = (w & 0x00FFFFFFu) | (kPadChar << 24);
+  return w;
+}
+
+// --------------------------------------------------------------- decode
+// One quad of Algorithm 2's main loop: four characters (little-endian word)
+// -> 24-bit value a*2^18 + b*2^12 + c*2^6 + d; err collects the table flags.
+__device__ __forceinline__ uint32_t dec_quad(uint32_t x, const uint8_t* D, uint32_t& err) {
+  const uint32_t a = D[x & 0xFFu];
+  const uint32_t b = D[(x >> 8) & 0xFFu];
+  const uint32_t c = D[(x >> 16) & 0xFFu];
+  const uint32_t d = D[x >> 24];
+  err |= a | b | c | d;
+  return (((((a << 6) | b) << 6) | c) << 6) | d;
+}
+
+// Four quads (16 characters) -> 12 output bytes (three little-endian words).
+__device__ __forceinline__ uint3 dec_unit(uint4 w, const uint8_t* D, uint32_t& err) {
+  const uint32_t v0 = dec_quad(w.x, D, err);
+  const uint32_t v1 = dec_quad(w.y, D, err);
+  const uint32_t v2 = dec_quad(w.z, D, err);
+  const uint32_t v3 = dec_quad(w.w, D, err);
+  uint3 o;
+  o.x = __byte_perm(v0, v1, 0x6012);
+  o.y = __byte_perm(v1, v2, 0x5601);
+  o.z = __byte_perm(v2, v3, 0x4560);
+  return o;
+}
+
+// Index (0..15) of the first character of a unit whose table entry is
+// flagged, or 16 if none.
+__device__ __forceinline__ uint32_t dec_unit_first_bad(uint4 w, const uint8_t* D) {
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (uint32_t k = 0; k < 16; ++k) {
+    const uint32_t ch = (ws[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+    if (D[ch] & kBadFlag) return k;
+  }
+  return 16;
+}
+
+// ---------------------------------------------------- unaligned access
+// Four little-endian words holding bytes p[0..15], for any alignment of p.
+// Aligned words are read only when they lie inside [lo, hi); near the ends
+// of the buffer single bytes are read instead.
+__device__ __forceinline__ uint4 load16_any(const uint8_t* p, const uint8_t* lo,
+                                            const uint8_t* hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t r = a & 3u;
+  uint4 v;
+  if (r == 0) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+    if ((a & 15u) == 0) return __ldg(reinterpret_cast<const uint4*>(p));
+    v.x = __ldg(q);
+    v.y = __ldg(q + 1);
+    v.z = __ldg(q + 2);
+    v.w = __ldg(q + 3);
+    return v;
+  }
+  const uint8_t* base = p - r;
+  if (base >= lo && base + 20 <= hi) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(base);
+    const uint32_t q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3),
+                   q4 = __ldg(q + 4);
+    const uint32_t sh = 8 * r;
+    v.x = __funnelshift_r(q0, q1, sh);
+    v.y = __funnelshift_r(q1, q2, sh);
+    v.z = __funnelshift_r(q2, q3, sh);
+    v.w = __funnelshift_r(q3, q4, sh);
+    return v;
+  }
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[k] = (uint32_t)__ldg(p + 4 * k) | ((uint32_t)__ldg(p + 4 * k + 1) << 8) |
+           ((uint32_t)__ldg(p + 4 * k + 2) << 16) | ((uint32_t)__ldg(p + 4 * k + 3) << 24);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Three little-endian words holding bytes p[0..11] (same rules).
+__device__ __forceinline__ uint3 load12_any(const uint8_t* p, const uint8_t* lo,
+                                            const uint8_t* hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t r = a & 3u;
+  uint3 v;
+  if (r == 0) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+    v.x = __ldg(q);
+    v.y = __ldg(q + 1);
+    v.z = __ldg(q + 2);
+    return v;
+  }
+  const uint8_t* base = p - r;
+  if (base >= lo && base + 16 <= hi) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(base);
+    const uint32_t q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
+    const uint32_t sh = 8 * r;
+    v.x = __funnelshift_r(q0, q1, sh);
+    v.y = __funnelshift_r(q1, q2, sh);
+    v.z = __funnelshift_r(q2, q3, sh);
+    return v;
+  }
+  uint32_t w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    w[k] = (uint32_t)__ldg(p + 4 * k) | ((uint32_t)__ldg(p + 4 * k + 1) << 8) |
+           ((uint32_t)__ldg(p + 4 * k + 2) << 16) | ((uint32_t)__ldg(p + 4 * k + 3) << 24);
+  }
+  return make_uint3(w[0], w[1], w[2]);
+}
+
+// Stores of 16 / 12 / 4 bytes at any alignment.
+__device__ __forceinline__ void store16_any(uint8_t* p, uint4 v) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  if ((a & 15u) == 0) {
+    *reinterpret_cast<uint4*>(p) = v;
+  } else if ((a & 3u) == 0) {
+    uint32_t* q = reinterpret_cast<uint32_t*>(p);
+    q[0] = v.x;
+    q[1] = v.y;
+    q[2] = v.z;
+    q[3] = v.w;
+  } else {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) p[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+  }
+}
+
+__device__ __forceinline__ void store12_any(uint8_t* p, uint3 v) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  if ((a & 3u) == 0) {
+    uint32_t* q = reinterpret_cast<uint32_t*>(p);
+    q[0] = v.x;
+    q[1] = v.y;
+    q[2] = v.z;
+  } else {
+    const uint32_t w[3] = {v.x, v.y, v.z};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+  }
+}
+
+__device__ __forceinline__ void store4_any(uint8_t* p, uint32_t w) {
+  if ((reinterpret_cast<uintptr_t>(p) & 3u) == 0) {
+    *reinterpret_cast<uint32_t*>(p) = w;
+  } else {
+    p[0] = (uint8_t)w;
+    p[1] = (uint8_t)(w >> 8);
+    p[2] = (uint8_t)(w >> 16);
+    p[3] = (uint8_t)(w >> 24);
+  }
+}
+
+// ------------------------------------------------------ error reduction
+// Lowers *target to min over the warp's lanes of idx (lanes pass
+// UINT64_MAX for "none"). One atomic per warp that saw an error.
+// Every lane of the warp must call it (it is a warp-wide convergence point).
+__device__ __forceinline__ void warp_min_to(unsigned long long* target, unsigned long long idx) {
+  const unsigned mask = 0xFFFFFFFFu;
+  const bool any = __ballot_sync(mask, idx != ~0ull) != 0;
+  if (!any) return;
+  // 64-bit min in two 32-bit reduction steps
+  const uint32_t hi = (uint32_t)(idx >> 32);
+  const uint32_t min_hi = __reduce_min_sync(mask, hi);
+  const uint32_t lo = (hi == min_hi) ? (uint32_t)idx : 0xFFFFFFFFu;
+  const uint32_t min_lo = __reduce_min_sync(mask, lo);
+  const unsigned long long m = ((unsigned long long)min_hi << 32) | min_lo;
+  if ((threadIdx.x & 31u) == 0) atomicMin(target, m);
+}
+
+}  // namespace gb64

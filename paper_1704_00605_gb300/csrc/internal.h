@@ -1,0 +1,65 @@
+// Internal interfaces between the translation units of libgb64 (not part of
+// the public C ABI, which is include/gb64.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gb64.h"
+
+namespace gb64 {
+
+// Records the calling thread's last error text (read by b64_last_error).
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Maps a CUDA failure to B64_ERR_CUDA (or B64_ERR_NOMEM) and records it.
+int cuda_status(cudaError_t e, const char* what);
+
+// Per-device facts used to size grids (cached; current device).
+struct DeviceInfo {
+  int device = -1;
+  int sm_count = 0;
+  int max_smem_optin = 0;
+  int cc_major = 0, cc_minor = 0;
+};
+const DeviceInfo* device_info(cudaError_t* err);
+
+// Kernel shape of a pipelined single-buffer launch.
+struct TileConfig {
+  int threads;  // 128, 256 or 512
+  int upt;      // units per thread per tile (encode unit 12 B, decode unit 16 chars)
+  int stages;   // input stages in shared memory (2..8)
+};
+
+// Default shapes (the tuner may pick others).
+TileConfig default_encode_config();
+TileConfig default_decode_config();
+
+// Single-buffer encode of n >= 1 bytes; picks the TMA kernel when src and
+// dst are 16-byte aligned, else the generic one.
+cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStream_t stream,
+                          const TileConfig& cfg);
+
+// Single-buffer decode of m characters. Characters [0, body_end) must be
+// whole quads of the alphabet; [body_end, m) are the final characters
+// (padding rules). The caller has set *res to all-ones bytes on stream.
+cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
+                          b64_result* res, cudaStream_t stream, const TileConfig& cfg);
+
+// Start of the final characters of a whole message of m characters.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint64_t decode_body_end(uint64_t m) {
+  if (m == 0) return 0;
+  return (m % 4 == 0) ? m - 4 : m - m % 4;
+}
+
+// Reads and clears the fault words of every kernel file (current device).
+int read_and_clear_faults();
+int batch_read_and_clear_fault(unsigned int* out);
+int single_read_and_clear_fault(unsigned int* out);
+
+}  // namespace gb64

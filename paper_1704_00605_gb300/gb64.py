@@ -1,0 +1,299 @@
+"""Thin ctypes binding of libgb64 (the C ABI in include/gb64.h).
+
+Every function here only marshals arguments: it allocates output tensors
+with torch when the caller did not pass them, turns tensors into raw device
+pointers and the current torch stream into a ``cudaStream_t``, and calls the
+C entry point of the same name. All coding runs in the library's CUDA
+kernels; when ``libgb64.so`` is missing, loading raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+B64_OK = 0
+B64_ERR_INVALID_CHAR = 1
+B64_ERR_BAD_LENGTH = 2
+B64_ERR_ARG = -1
+B64_ERR_CUDA = -2
+B64_ERR_NOMEM = -3
+B64_ERR_TIMEOUT = -4
+SIZE_MAX = (1 << 64) - 1
+
+_lib = None
+
+
+class Gb64Error(RuntimeError):
+    """A call of the C ABI returned an error code."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libgb64.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1704_00605_gb300.build.build(); "
+                           "the codec has no CPU fallback")
+    L = ctypes.CDLL(path)
+    sz, vp, i64, i32 = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    psz = ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "b64_encoded_len": (sz, [sz]),
+        "b64_decoded_cap": (sz, [sz]),
+        "b64_encode": (sz, [vp, sz, vp, vp]),
+        "b64_decode": (i32, [vp, sz, vp, psz, psz, vp]),
+        "b64_decode_async": (i32, [vp, sz, vp, vp, vp]),
+        "b64_encode_host": (sz, [vp, sz, vp, vp]),
+        "b64_decode_host": (i32, [vp, sz, vp, psz, psz, vp]),
+        "b64_batch_out_offsets": (i32, [i32, vp, i64, vp, vp]),
+        "b64_encode_batch": (i32, [vp, vp, i64, vp, vp, vp]),
+        "b64_decode_batch": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp]),
+        "b64_status_str": (ctypes.c_char_p, [i32]),
+        "b64_last_error": (ctypes.c_char_p, []),
+        "b64_device_fault": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_name(status: int) -> str:
+    try:
+        return lib().b64_status_str(status).decode()
+    except Exception:
+        return str(status)
+
+
+def b64_last_error() -> str:
+    return lib().b64_last_error().decode()
+
+
+def b64_status_str(status: int) -> str:
+    return lib().b64_status_str(status).decode()
+
+
+def b64_encoded_len(n: int) -> int:
+    return int(lib().b64_encoded_len(n))
+
+
+def b64_decoded_cap(m: int) -> int:
+    return int(lib().b64_decoded_cap(m))
+
+
+def b64_device_fault() -> int:
+    return int(lib().b64_device_fault())
+
+
+# ------------------------------------------------------------ marshalling
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if t is not None and t.numel() else 0
+
+
+def _stream(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_u8(t, name):
+    torch = _torch()
+    if t.dtype != torch.uint8 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous uint8 CUDA tensor")
+
+
+def b64_encode(src, dst=None, stream=None):
+    """Encode ``src`` (uint8 CUDA tensor); returns the characters (uint8)."""
+    torch = _torch()
+    _check_u8(src, "src")
+    n = src.numel()
+    m = b64_encoded_len(n)
+    if dst is None:
+        dst = torch.empty(m, dtype=torch.uint8, device=src.device)
+    _check_u8(dst, "dst")
+    if dst.numel() < m:
+        raise ValueError("dst is too small")
+    with torch.cuda.device(src.device):
+        r = lib().b64_encode(_ptr(src), n, _ptr(dst), _stream(stream, src.device))
+    if r == SIZE_MAX:
+        raise Gb64Error(B64_ERR_ARG, b64_last_error())
+    return dst[:m]
+
+
+def b64_decode(src, dst=None, stream=None):
+    """Synchronous decode. Returns ``(status, outlen, first_bad, dst)``."""
+    torch = _torch()
+    _check_u8(src, "src")
+    m = src.numel()
+    cap = b64_decoded_cap(m)
+    if dst is None:
+        dst = torch.empty(max(cap, 1), dtype=torch.uint8, device=src.device)
+    _check_u8(dst, "dst")
+    outlen = ctypes.c_size_t(0)
+    first_bad = ctypes.c_size_t(0)
+    with torch.cuda.device(src.device):
+        st = lib().b64_decode(_ptr(src), m, _ptr(dst) if cap else 0, ctypes.byref(outlen),
+                              ctypes.byref(first_bad), _stream(stream, src.device))
+    if st < 0:
+        raise Gb64Error(st, b64_last_error())
+    return st, int(outlen.value), int(first_bad.value), dst
+
+
+def b64_decode_async(src, dst, result, stream=None):
+    """Enqueue a decode; ``result`` is an int64 CUDA tensor of 3 entries that
+    receives (first_bad, outlen, status | internal << 32)."""
+    torch = _torch()
+    _check_u8(src, "src")
+    if result.dtype != torch.int64 or result.numel() < 3 or not result.is_cuda:
+        raise ValueError("result must be an int64 CUDA tensor with 3 entries")
+    m = src.numel()
+    with torch.cuda.device(src.device):
+        st = lib().b64_decode_async(_ptr(src), m, _ptr(dst) if b64_decoded_cap(m) else 0,
+                                    result.data_ptr(), _stream(stream, src.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+
+
+def parse_result(result) -> tuple:
+    """(status, outlen, first_bad) from a result tensor of b64_decode_async."""
+    r = result.cpu().numpy()
+    status = int(np.int32(r[2] & 0xFFFFFFFF))
+    return status, int(r[1]), int(r[0])
+
+
+def _host_u8(a) -> np.ndarray:
+    if isinstance(a, (bytes, bytearray, memoryview)):
+        a = np.frombuffer(bytes(a), dtype=np.uint8)
+    if hasattr(a, "numpy") and not isinstance(a, np.ndarray):  # torch CPU tensor
+        a = a.numpy()
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.uint8:
+        a = a.view(np.uint8)
+    return a
+
+
+def b64_encode_host(h_src, h_dst=None, stream=None):
+    """Encode host memory (numpy/bytes/CPU tensor); returns a numpy array."""
+    torch = _torch()
+    src = _host_u8(h_src)
+    m = b64_encoded_len(src.size)
+    dst = np.empty(max(m, 1), dtype=np.uint8) if h_dst is None else _host_u8(h_dst)
+    r = lib().b64_encode_host(src.ctypes.data if src.size else 0, src.size, dst.ctypes.data,
+                              _stream(stream, torch.cuda.current_device()))
+    if r == SIZE_MAX:
+        raise Gb64Error(B64_ERR_ARG, b64_last_error())
+    return dst[:m]
+
+
+def b64_decode_host(h_src, h_dst=None, stream=None):
+    """Decode host memory; returns ``(status, outlen, first_bad, dst)``."""
+    torch = _torch()
+    src = _host_u8(h_src)
+    cap = b64_decoded_cap(src.size)
+    dst = np.empty(max(cap, 1), dtype=np.uint8) if h_dst is None else _host_u8(h_dst)
+    outlen = ctypes.c_size_t(0)
+    first_bad = ctypes.c_size_t(0)
+    st = lib().b64_decode_host(src.ctypes.data if src.size else 0, src.size, dst.ctypes.data,
+                               ctypes.byref(outlen), ctypes.byref(first_bad),
+                               _stream(stream, torch.cuda.current_device()))
+    if st < 0:
+        raise Gb64Error(st, b64_last_error())
+    return st, int(outlen.value), int(first_bad.value), dst
+
+
+def _nonempty(t):
+    """A tensor with a valid device pointer: batches of empty messages still
+    pass real buffers to the C ABI."""
+    torch = _torch()
+    return t if t.numel() else torch.empty(1, dtype=t.dtype, device=t.device)
+
+
+def _check_off(t, name):
+    torch = _torch()
+    if t.dtype != torch.int64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous int64 CUDA tensor")
+
+
+def b64_batch_out_offsets(decode: bool, in_off, out_off=None, stream=None):
+    """Output offsets (exclusive prefix of encoded lengths or decode
+    capacities) of packed messages; returns an int64 CUDA tensor."""
+    torch = _torch()
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
+    with torch.cuda.device(in_off.device):
+        st = lib().b64_batch_out_offsets(1 if decode else 0, in_off.data_ptr(), nmsg,
+                                         out_off.data_ptr(), _stream(stream, in_off.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return out_off
+
+
+def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None):
+    """Encode packed messages; returns ``(dst, out_off)``."""
+    torch = _torch()
+    _check_u8(src, "src")
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
+    if dst is None:
+        b64_batch_out_offsets(False, in_off, out_off, stream)
+        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=src.device)
+    with torch.cuda.device(src.device):
+        src, dst = _nonempty(src), _nonempty(dst)
+        st = lib().b64_encode_batch(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
+                                    out_off.data_ptr(), _stream(stream, src.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return dst, out_off
+
+
+def b64_decode_batch(src, in_off, dst=None, out_off=None, status=None, first_bad=None,
+                     outlen=None, stream=None):
+    """Decode packed messages; returns ``(dst, out_off, status, first_bad, outlen)``."""
+    torch = _torch()
+    _check_u8(src, "src")
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    dev = src.device
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=dev)
+    if dst is None:
+        b64_batch_out_offsets(True, in_off, out_off, stream)
+        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=dev)
+    if status is None:
+        status = torch.empty(max(nmsg, 1), dtype=torch.int32, device=dev)
+    if first_bad is None:
+        first_bad = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev)
+    if outlen is None:
+        outlen = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev)
+    with torch.cuda.device(dev):
+        src, dst = _nonempty(src), _nonempty(dst)
+        st = lib().b64_decode_batch(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
+                                    out_off.data_ptr(), status.data_ptr(), first_bad.data_ptr(),
+                                    outlen.data_ptr(), _stream(stream, dev))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return dst, out_off, status[:nmsg], first_bad[:nmsg], outlen[:nmsg]

@@ -1,0 +1,115 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; host-side argument checks run without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1704_00605_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gb64.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build.ensure_built()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(b64_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["b64_encode", "b64_decode", "b64_decode_async", "b64_encode_batch",
+              "b64_decode_batch", "b64_batch_out_offsets", "b64_encoded_len", "b64_decoded_cap",
+              "b64_encode_host", "b64_decode_host", "b64_status_str", "b64_last_error",
+              "b64_device_fault"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (b64_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_header_compiles_as_c(tmp_path):
+    c = tmp_path / "t.c"
+    c.write_text('#include "gb64.h"\nint main(void){return (int)b64_encoded_len(3) - 4;}\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-c", str(c), "-o", str(tmp_path / "t.o")], check=True)
+
+
+@pytest.fixture(scope="module")
+def g(libpath):
+    from paper_1704_00605_gb300 import gb64
+
+    gb64.lib()
+    return gb64
+
+
+def test_length_closed_forms(g):
+    for n in range(0, 100):
+        assert g.b64_encoded_len(n) == 4 * -(-n // 3)
+        assert g.b64_decoded_cap(n) == 3 * (n // 4)
+    assert g.b64_encoded_len((1 << 64) - 1) == g.SIZE_MAX
+    assert g.b64_encoded_len(1 << 30) == 1431655768
+    assert g.b64_encoded_len((1 << 30) + 2) == 1431655768
+
+
+def test_status_strings(g):
+    assert g.b64_status_str(0) == "B64_OK"
+    assert g.b64_status_str(1) == "B64_ERR_INVALID_CHAR"
+    assert g.b64_status_str(2) == "B64_ERR_BAD_LENGTH"
+    assert g.b64_status_str(-4) == "B64_ERR_TIMEOUT"
+    assert g.b64_status_str(99) == "B64_UNKNOWN_STATUS"
+
+
+def test_argument_errors_need_no_gpu(g):
+    L = g.lib()
+    # encode: null pointers, overlap; n = 0 is legal and enqueues nothing
+    assert L.b64_encode(None, 0, None, None) == 0
+    assert L.b64_encode(None, 5, None, None) == g.SIZE_MAX
+    assert "null" in g.b64_last_error()
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.addressof(buf)
+    assert L.b64_encode(p, 9, p + 4, None) == g.SIZE_MAX
+    assert "overlap" in g.b64_last_error()
+    # decode: null result pointers; m = 0 answers on the host
+    ol, fb = ctypes.c_size_t(7), ctypes.c_size_t(7)
+    assert L.b64_decode(None, 4, None, None, None, None) == g.B64_ERR_ARG
+    assert L.b64_decode(None, 0, None, ctypes.byref(ol), ctypes.byref(fb), None) == g.B64_OK
+    assert ol.value == 0 and fb.value == 0
+    assert L.b64_decode_async(p, 8, p + 16, None, None) == g.B64_ERR_ARG
+    assert L.b64_decode_async(p, 8, p + 16, p + 3, None) == g.B64_ERR_ARG  # misaligned result
+    assert L.b64_decode_async(p, 8, p + 4, p + 32, None) == g.B64_ERR_ARG  # overlap
+    # batch: negative count, null or misaligned offsets
+    assert L.b64_encode_batch(p, p, -1, p, p, None) == g.B64_ERR_ARG
+    assert L.b64_encode_batch(p, None, 3, p, p, None) == g.B64_ERR_ARG
+    assert L.b64_decode_batch(p, p + 4, 3, p, p, p, p, p, None) == g.B64_ERR_ARG
+    assert L.b64_batch_out_offsets(0, None, 1, p, None) == g.B64_ERR_ARG
+    # host forms
+    assert L.b64_encode_host(None, 3, None, None) == g.SIZE_MAX
+    assert L.b64_decode_host(p, 4, p, None, None, None) == g.B64_ERR_ARG
+    assert L.b64_decode_host(None, 0, None, ctypes.byref(ol), ctypes.byref(fb), None) == g.B64_OK
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1704_00605_gb300 import gb64
+
+    monkeypatch.setattr(gb64, "_lib", None)
+    monkeypatch.setattr(gb64._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gb64.lib()

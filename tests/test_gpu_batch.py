@@ -1,0 +1,164 @@
+"""GPU parity of the batched codec against the CPU oracle (exact).
+
+Each message's output, status, first_bad and outlen must equal the oracle's
+for that message alone; batches include empty and 1-byte messages, messages
+that straddle tiles, every length class mod 3 / mod 4, injected errors, and
+the batched workloads at reduced and full message counts.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_00605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype=None):
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.cuda() if dtype is None else t.to(dtype).cuda()
+
+
+def check_encode_batch(gb64, oracle, data, off):
+    dst, out_off = gb64.b64_encode_batch(dev(data), dev(off))
+    exp, exp_off = oracle.encode_batch(data, off)
+    assert np.array_equal(out_off.cpu().numpy(), exp_off)
+    assert np.array_equal(dst.cpu().numpy()[:exp.size], exp)
+    return exp, exp_off
+
+
+def check_decode_batch(gb64, oracle, chars, off):
+    dst, out_off, st, fb, ol = gb64.b64_decode_batch(dev(chars), dev(off))
+    edst, eoff, est, efb, eol = oracle.decode_batch(chars, off)
+    assert np.array_equal(out_off.cpu().numpy(), eoff)
+    st, fb, ol = st.cpu().numpy(), fb.cpu().numpy(), ol.cpu().numpy()
+    bad = np.nonzero((st != est) | (fb != efb) | (ol != eol))[0]
+    assert bad.size == 0, (bad[:5], st[bad[:5]], est[bad[:5]], fb[bad[:5]], efb[bad[:5]])
+    h = dst.cpu().numpy()
+    okm = np.nonzero(est == 0)[0]
+    for j in okm:
+        a, n = eoff[j], eol[j]
+        if n:
+            assert np.array_equal(h[a:a + n], edst[a:a + n]), j
+    return est, efb
+
+
+def test_small_mixed_batch(gb64, oracle):
+    lens = np.array([0, 1, 2, 3, 4, 5, 0, 11, 12, 13, 47, 48, 49, 6143, 6144, 6145, 20000, 0, 1,
+                     12289, 100000, 7], dtype=np.int64)
+    off = W.offsets_from_lengths(lens)
+    data = W.uniform_bytes(int(off[-1]), 9)
+    enc, eoff = check_encode_batch(gb64, oracle, data, off)
+    check_decode_batch(gb64, oracle, enc, eoff)
+
+
+def test_empty_and_single_message_batches(gb64, oracle):
+    import torch
+
+    off = np.zeros(1, dtype=np.int64)
+    dst, out_off = gb64.b64_encode_batch(dev(np.zeros(1, np.uint8)), dev(off))
+    assert out_off.cpu().tolist() == [0]
+    for n in [0, 1, 2, 3, 100, 65537]:
+        off = np.array([0, n], dtype=np.int64)
+        data = W.uniform_bytes(n, n)
+        enc, eoff = check_encode_batch(gb64, oracle, data, off)
+        check_decode_batch(gb64, oracle, enc, eoff)
+    _ = torch
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_batches(gb64, oracle, seed):
+    rng = np.random.default_rng(seed)
+    nmsg = int(rng.integers(1, 3000))
+    lens = W.lognormal_lengths(rng, nmsg, 300.0, 2.0, 0, 200_000)
+    off = W.offsets_from_lengths(lens)
+    data = W.uniform_bytes(int(off[-1]), seed)
+    enc, eoff = check_encode_batch(gb64, oracle, data, off)
+    check_decode_batch(gb64, oracle, enc, eoff)
+
+
+def test_decode_batch_arbitrary_lengths_and_bytes(gb64, oracle):
+    """Strings that are not encodings: random lengths (any mod 4) of mostly
+    alphabet characters with random '=' and other bytes mixed in."""
+    rng = np.random.default_rng(21)
+    alpha = np.array([oracle.table1_char(v) for v in range(64)], dtype=np.uint8)
+    nmsg = 4000
+    lens = rng.integers(0, 300, nmsg)
+    off = W.offsets_from_lengths(lens.astype(np.int64))
+    chars = alpha[rng.integers(0, 64, int(off[-1]))]
+    for j in range(nmsg):
+        a, b = off[j], off[j + 1]
+        r = rng.random()
+        if b - a >= 2 and r < 0.2:
+            chars[b - 2:b] = 0x3D
+        elif b - a >= 1 and r < 0.4:
+            chars[b - 1] = 0x3D
+        elif b > a and r < 0.5:
+            chars[int(rng.integers(a, b))] = int(rng.integers(0, 256))
+    check_decode_batch(gb64, oracle, chars, off)
+
+
+def test_workload_batched_reduced(gb64, oracle):
+    data, off = W.batched(nmsg=5000, seed=2)
+    enc, eoff = check_encode_batch(gb64, oracle, data, off)
+    check_decode_batch(gb64, oracle, enc, eoff)
+
+
+def test_workload_batched_full(gb64, oracle):
+    """100,000 messages (seed 2) through the shapes the benchmark times:
+    outputs equal the single-buffer calls on sampled messages and the oracle
+    on sampled messages; the decode round trip is exact for all."""
+    import torch
+
+    data, off = W.batched()
+    src, doff = dev(data), dev(off)
+    enc, eoff = gb64.b64_encode_batch(src, doff)
+    dst, out_off, st, fb, ol = gb64.b64_decode_batch(enc, eoff)
+    assert int((st != 0).sum()) == 0
+    lens = torch.diff(doff)
+    assert torch.equal(ol, lens)
+    eo = eoff.cpu().numpy()
+    oo = out_off.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for j in rng.integers(0, off.size - 1, 300):
+        raw = data[off[j]:off[j + 1]]
+        exp = oracle.encode(raw)
+        assert np.array_equal(enc[eo[j]:eo[j + 1]].cpu().numpy(), exp)
+        single = gb64.b64_encode(src[int(off[j]):int(off[j + 1])])
+        assert np.array_equal(single.cpu().numpy(), exp)
+        assert np.array_equal(dst[oo[j]:oo[j] + raw.size].cpu().numpy(), raw)
+    # every decoded message equals its payload: compare packed views
+    keep = torch.zeros(int(oo[-1]), dtype=torch.bool, device="cuda")
+    starts = out_off[:-1]
+    idx = torch.repeat_interleave(starts, lens) + (
+        torch.arange(int(lens.sum()), device="cuda") -
+        torch.repeat_interleave(doff[:-1], lens))
+    keep[idx] = True
+    assert torch.equal(dst[:int(oo[-1])][keep], src)
+
+
+def test_workload_error_batch_reduced(gb64, oracle):
+    """Config 4 recipe at 20,000 messages: per-message status and first_bad
+    exactly as the oracle's."""
+    rec = W.error_batch(nmsg=20_000, seed=3)
+    off = rec["in_off"]
+    payload = W.counter_bytes(rec["payload_key"], 0, int(off[-1]))
+    enc, eoff = oracle.encode_batch(payload, off)
+    genc, geoff = gb64.b64_encode_batch(dev(payload), dev(off))
+    assert np.array_equal(genc.cpu().numpy(), enc)
+    W.inject_errors(enc, eoff, rec["err_msg"], rec["err_frac"], rec["err_byte"])
+    est, efb = check_decode_batch(gb64, oracle, enc, eoff)
+    assert (est != 0).sum() == rec["err_msg"].size
+
+
+def test_batch_deterministic_and_stream_ordered(gb64, oracle):
+    import torch
+
+    data, off = W.batched(nmsg=3000, seed=7)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a, ao = gb64.b64_encode_batch(dev(data), dev(off), stream=s)
+        b, bo = gb64.b64_encode_batch(dev(data), dev(off), stream=s)
+    s.synchronize()
+    assert torch.equal(a, b) and torch.equal(ao, bo)
