@@ -119,6 +119,22 @@ int b64_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg, uint8
                      int64_t *out_off, int32_t *status, int64_t *first_bad, int64_t *outlen,
                      gb64_stream_t stream);
 
+/* Batched decode that allocates nothing. The paper has no counterpart: this
+ * is an interface for callers that must not allocate device memory inside
+ * the call (a fixed memory budget or an allocator owned by someone else, or
+ * a hot path that cannot afford cudaMalloc/cudaFree synchronizing the
+ * device). Same arguments, kernels and results as b64_decode_batch, but the
+ * scratch lives in a fixed array inside the library (about 576 KiB per GPU
+ * that uses it, held until the process exits) instead of coming from the
+ * stream-ordered allocator. At most 65536 messages per call; a larger nmsg
+ * returns B64_ERR_ARG with nothing enqueued. Every call on a device shares
+ * that array, so two calls that overlap on the GPU race: order them on one
+ * stream or with events. The first call on a device looks up the array's
+ * device address; make it before any stream capture. Asynchronous. */
+int b64_decode_batch_noalloc(const char *src, const int64_t *in_off, int64_t nmsg, uint8_t *dst,
+                             int64_t *out_off, int32_t *status, int64_t *first_bad,
+                             int64_t *outlen, gb64_stream_t stream);
+
 /* Human-readable name of a b64_status value (static string). */
 const char *b64_status_str(int status);
 
