@@ -135,6 +135,51 @@ int b64_decode_batch_noalloc(const char *src, const int64_t *in_off, int64_t nms
                              int64_t *out_off, int32_t *status, int64_t *first_bad,
                              int64_t *outlen, gb64_stream_t stream);
 
+/* ---- launch shapes and the autotuner (no counterpart in the paper) ----
+ * Kernel families: */
+enum {
+  B64_KIND_ENCODE = 0,       /* b64_encode and the host-buffer encode */
+  B64_KIND_DECODE = 1,       /* b64_decode(_async) and the host-buffer decode */
+  B64_KIND_ENCODE_BATCH = 2, /* b64_encode_batch */
+  B64_KIND_DECODE_BATCH = 3  /* b64_decode_batch(_noalloc) */
+};
+
+/* A launch shape. Single kinds use threads, units_per_thread (12 input
+ * bytes or 16 characters each; tile = threads * units_per_thread * unit),
+ * stages (TMA stages in shared memory) and blocks_per_sm (0 = as many as
+ * fit). Batch kinds use threads, tile (input bytes, multiple of 48, or
+ * characters, multiple of 64) and blocks_per_sm. ms is a measured time. */
+typedef struct {
+  int32_t threads;
+  int32_t units_per_thread;
+  int32_t stages;
+  int32_t blocks_per_sm;
+  int64_t tile;
+  float ms;
+} b64_shape;
+
+/* Shapes are kept per size bucket: single kinds by input size (total =
+ * bytes or characters; nmsg ignored), batch kinds by mean message length
+ * (total / nmsg; total < 0 = unknown). b64_shape_get returns the shape a
+ * call of that size uses; b64_shape_set replaces it (B64_ERR_ARG if the
+ * shape is not valid for the kind). */
+int b64_shape_get(int kind, int64_t total, int64_t nmsg, b64_shape *out);
+int b64_shape_set(int kind, int64_t total, int64_t nmsg, const b64_shape *shape);
+
+/* Autotune one bucket: generate `total` bytes (or characters) of random
+ * test data on the device (as nmsg messages for batch kinds), time every
+ * candidate shape of the kind with CUDA events (median of 7 runs), and keep
+ * the fastest for that bucket. Up to max_trials timed shapes are written to
+ * trials (host array, may be null) and their count to *ntrials. Allocates
+ * its test buffers; synchronous on stream. */
+int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape *trials, int max_trials,
+             int *ntrials, gb64_stream_t stream);
+
+/* Write / read the shape table (text). The file named by the environment
+ * variable GB64_TUNE_FILE, if set, is read at first use. */
+int b64_tune_save(const char *path);
+int b64_tune_load(const char *path);
+
 /* Human-readable name of a b64_status value (static string). */
 const char *b64_status_str(int status);
 

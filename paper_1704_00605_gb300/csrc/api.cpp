@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tuner.h"
 
 namespace gb64 {
 
@@ -128,7 +129,7 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
   cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(b64_result), stream);
   if (e != cudaSuccess) return cuda_status(e, "decode: clearing the result");
   e = launch_decode(reinterpret_cast<const uint8_t*>(src), m, decode_body_end(m), dst, d_result,
-                    stream, default_decode_config());
+                    stream, single_config(1, m));
   if (e != cudaSuccess) return cuda_status(e, "decode: launch");
   return B64_OK;
 }
@@ -164,7 +165,7 @@ size_t b64_encode(const uint8_t* src, size_t n, char* dst, gb64_stream_t stream)
     return SIZE_MAX;
   }
   cudaError_t e = launch_encode(src, n, reinterpret_cast<uint8_t*>(dst),
-                                reinterpret_cast<cudaStream_t>(stream), default_encode_config());
+                                reinterpret_cast<cudaStream_t>(stream), single_config(0, n));
   if (e != cudaSuccess) {
     cuda_status(e, "encode: launch");
     return SIZE_MAX;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tuner.h"
 
 namespace gb64 {
 
@@ -129,7 +130,7 @@ size_t b64_encode_host(const uint8_t* h_src, size_t n, char* h_dst, gb64_stream_
     const int b = (int)(i & 1);
     const size_t len = std::min(chunk, n - off);
     e = cudaMemcpyAsync(p->in[b], h_src + off, len, cudaMemcpyHostToDevice, p->st[b]);
-    if (e == cudaSuccess) e = launch_encode(p->in[b], len, p->out[b], p->st[b], default_encode_config());
+    if (e == cudaSuccess) e = launch_encode(p->in[b], len, p->out[b], p->st[b], single_config(0, len));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h_dst + off / 3 * 4, p->out[b], b64_encoded_len(len),
                           cudaMemcpyDeviceToHost, p->st[b]);
@@ -180,7 +181,7 @@ int b64_decode_host(const char* h_src, size_t m, uint8_t* h_dst, size_t* outlen,
     if (e == cudaSuccess) e = cudaMemsetAsync(p->res + i, 0xFF, sizeof(b64_result), p->st[b]);
     if (e == cudaSuccess)
       e = launch_decode(p->in[b], len, last ? body_end - off : len, p->out[b], p->res + i,
-                        p->st[b], default_decode_config());
+                        p->st[b], single_config(1, len));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h_dst + off / 4 * 3, p->out[b], b64_decoded_cap(len),
                           cudaMemcpyDeviceToHost, p->st[b]);

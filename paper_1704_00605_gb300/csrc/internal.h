@@ -28,9 +28,10 @@ const DeviceInfo* device_info(cudaError_t* err);
 
 // Kernel shape of a pipelined single-buffer launch.
 struct TileConfig {
-  int threads;  // 128, 256 or 512
-  int upt;      // units per thread per tile (encode unit 12 B, decode unit 16 chars)
-  int stages;   // input stages in shared memory (2..8)
+  int threads;            // 128, 256 or 512
+  int upt;                // units per thread per tile (encode unit 12 B, decode unit 16 chars)
+  int stages;             // input stages in shared memory (2..8)
+  int blocks_per_sm = 0;  // persistent CTAs per SM (0 = as many as fit)
 };
 
 // Default shapes (the tuner may pick others).

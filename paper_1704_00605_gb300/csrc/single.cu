@@ -408,8 +408,8 @@ __global__ void __launch_bounds__(NT) k_decode_any(DecArgs a) {
 }
 
 // ------------------------------------------------------------------ host
-TileConfig default_encode_config() { return TileConfig{256, 4, 4}; }
-TileConfig default_decode_config() { return TileConfig{256, 4, 3}; }
+TileConfig default_encode_config() { return TileConfig{256, 4, 4, 0}; }
+TileConfig default_decode_config() { return TileConfig{256, 4, 3, 0}; }
 
 namespace {
 
@@ -423,7 +423,11 @@ cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm
 
 bool valid_config(const TileConfig& c) {
   return (c.threads == 128 || c.threads == 256 || c.threads == 512) && c.upt >= 1 &&
-         c.upt <= 16 && c.stages >= 2 && c.stages <= kMaxStages;
+         c.upt <= 16 && c.stages >= 2 && c.stages <= kMaxStages && c.blocks_per_sm >= 0;
+}
+
+int resident_ctas(int fitting, const TileConfig& c) {
+  return c.blocks_per_sm > 0 ? std::min(fitting, c.blocks_per_sm) : fitting;
 }
 
 template <int NT>
@@ -440,7 +444,8 @@ cudaError_t launch_encode_nt(const uint8_t* src, uint64_t n, uint8_t* dst, cudaS
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = (n + tile_in - 1) / tile_in;
-    const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * bps);
+    const int grid =
+        (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * resident_ctas(bps, cfg));
     k_encode_tma<NT><<<grid, NT, smem, stream>>>(a);
     return cudaGetLastError();
   }
@@ -468,7 +473,8 @@ cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileC
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = std::max<uint64_t>(1, (a.m + tile_c - 1) / tile_c);
-    const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * bps);
+    const int grid =
+        (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * resident_ctas(bps, cfg));
     k_decode_tma<NT><<<grid, NT, smem, stream>>>(a);
     return cudaGetLastError();
   }

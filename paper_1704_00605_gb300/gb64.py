@@ -27,6 +27,22 @@ SIZE_MAX = (1 << 64) - 1
 
 _lib = None
 
+B64_KIND_ENCODE = 0
+B64_KIND_DECODE = 1
+B64_KIND_ENCODE_BATCH = 2
+B64_KIND_DECODE_BATCH = 3
+
+
+class b64_shape(ctypes.Structure):
+    """Launch shape (mirrors ``b64_shape`` in include/gb64.h)."""
+
+    _fields_ = [("threads", ctypes.c_int32), ("units_per_thread", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("tile", ctypes.c_int64), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 
 class Gb64Error(RuntimeError):
     """A call of the C ABI returned an error code."""
@@ -62,6 +78,12 @@ def lib() -> ctypes.CDLL:
         "b64_status_str": (ctypes.c_char_p, [i32]),
         "b64_last_error": (ctypes.c_char_p, []),
         "b64_device_fault": (i32, []),
+        "b64_shape_get": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
+        "b64_shape_set": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
+        "b64_tune": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape), i32,
+                           ctypes.POINTER(ctypes.c_int), vp]),
+        "b64_tune_save": (i32, [ctypes.c_char_p]),
+        "b64_tune_load": (i32, [ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -297,3 +319,43 @@ def b64_decode_batch(src, in_off, dst=None, out_off=None, status=None, first_bad
     if st != B64_OK:
         raise Gb64Error(st, b64_last_error())
     return dst, out_off, status[:nmsg], first_bad[:nmsg], outlen[:nmsg]
+
+
+# ------------------------------------------------------------------ tuner
+def b64_shape_get(kind: int, total: int, nmsg: int = 1) -> dict:
+    out = b64_shape()
+    st = lib().b64_shape_get(kind, total, nmsg, ctypes.byref(out))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return out.as_dict()
+
+
+def b64_shape_set(kind: int, total: int, nmsg: int = 1, **shape) -> None:
+    cur = b64_shape(**{k: v for k, v in b64_shape_get(kind, total, nmsg).items()})
+    for k, v in shape.items():
+        setattr(cur, k, v)
+    st = lib().b64_shape_set(kind, total, nmsg, ctypes.byref(cur))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+
+
+def b64_tune(kind: int, total: int, nmsg: int = 1, stream=None, max_trials: int = 256):
+    """Autotune the bucket of (kind, total, nmsg); returns the timed trials."""
+    torch = _torch()
+    trials = (b64_shape * max_trials)()
+    n = ctypes.c_int(0)
+    st = lib().b64_tune(kind, total, nmsg, trials, max_trials, ctypes.byref(n),
+                        _stream(stream, torch.cuda.current_device()))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return [trials[i].as_dict() for i in range(n.value)]
+
+
+def b64_tune_save(path: str) -> None:
+    if lib().b64_tune_save(path.encode()) != B64_OK:
+        raise Gb64Error(B64_ERR_ARG, b64_last_error())
+
+
+def b64_tune_load(path: str) -> None:
+    if lib().b64_tune_load(path.encode()) != B64_OK:
+        raise Gb64Error(B64_ERR_ARG, b64_last_error())

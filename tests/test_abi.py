@@ -113,3 +113,25 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gb64._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         gb64.lib()
+
+
+def test_shape_table_host_side(g, tmp_path):
+    """The shape table (no GPU needed): defaults, set/get per bucket,
+    rejection of invalid shapes, save/load round trip."""
+    d = g.b64_shape_get(g.B64_KIND_ENCODE, 1 << 30)
+    assert d["threads"] in (128, 256, 512) and d["tile"] == d["threads"] * d["units_per_thread"] * 12
+    g.b64_shape_set(g.B64_KIND_ENCODE, 1 << 20, threads=128, units_per_thread=2, stages=3)
+    assert g.b64_shape_get(g.B64_KIND_ENCODE, (1 << 20) + 5)["threads"] == 128  # same bucket
+    assert g.b64_shape_get(g.B64_KIND_ENCODE, 1 << 30)["threads"] == d["threads"]  # other bucket
+    with pytest.raises(g.Gb64Error):
+        g.b64_shape_set(g.B64_KIND_ENCODE, 1 << 20, threads=100)
+    with pytest.raises(g.Gb64Error):
+        g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=256, tile=1000)
+    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=512, tile=512 * 16, blocks_per_sm=4)
+    path = str(tmp_path / "shapes.txt")
+    g.b64_tune_save(path)
+    text = open(path).read()
+    assert "512" in text and "128" in text
+    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=256, tile=256 * 16, blocks_per_sm=8)
+    g.b64_tune_load(path)
+    assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["threads"] == 512

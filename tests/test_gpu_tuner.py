@@ -1,0 +1,77 @@
+"""The autotuner: it times every candidate shape, keeps the fastest for the
+bucket, and every candidate shape it may pick codes bit-exactly (checked
+against the oracle with the shape forced for its bucket)."""
+import numpy as np
+import pytest
+
+from paper_1704_00605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def restore_shapes(gb64, tmp_path):
+    path = str(tmp_path / "before.txt")
+    gb64.b64_tune_save(path)
+    yield
+    gb64.b64_tune_load(path)
+
+
+def _check_single(gb64, oracle, raw):
+    import torch
+
+    src = torch.from_numpy(raw).cuda()
+    enc = gb64.b64_encode(src)
+    exp = oracle.encode(raw)
+    assert np.array_equal(enc.cpu().numpy(), exp)
+    st, outlen, fb, dst = gb64.b64_decode(enc)
+    assert (st, outlen, fb) == (0, raw.size, exp.size)
+    assert torch.equal(dst[:outlen], src)
+    bad = enc.clone()
+    p = exp.size - 3 * exp.size // 7
+    bad[p] = 0x2A
+    st, outlen, fb, _ = gb64.b64_decode(bad)
+    assert (st, fb) == (1, p)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tune_single_and_every_candidate_is_exact(gb64, oracle, restore_shapes, kind):
+    size = 3 << 20  # the 1-16 MiB bucket
+    trials = gb64.b64_tune(kind, size)
+    assert len(trials) >= 20 and all(t["ms"] > 0 for t in trials)
+    best = min(trials, key=lambda t: t["ms"])
+    got = gb64.b64_shape_get(kind, size)
+    assert (got["threads"], got["units_per_thread"], got["stages"], got["blocks_per_sm"]) == \
+        (best["threads"], best["units_per_thread"], best["stages"], best["blocks_per_sm"])
+    n = 3 * (1 << 20) // 4 * 3 + 7 if kind == 1 else (3 << 20) + 2
+    raw = W.uniform_bytes(n, 40 + kind)
+    for t in trials:
+        gb64.b64_shape_set(0, n, threads=t["threads"], units_per_thread=t["units_per_thread"],
+                           stages=t["stages"], blocks_per_sm=t["blocks_per_sm"])
+        gb64.b64_shape_set(1, gb64.b64_encoded_len(n), threads=t["threads"],
+                           units_per_thread=t["units_per_thread"], stages=t["stages"],
+                           blocks_per_sm=t["blocks_per_sm"])
+        _check_single(gb64, oracle, raw)
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_tune_batch_and_every_candidate_is_exact(gb64, oracle, restore_shapes, kind):
+    import torch
+
+    data, off = W.batched(nmsg=1500, seed=50 + kind, median=1500.0)
+    total, nmsg = int(off[-1]), off.size - 1
+    trials = gb64.b64_tune(kind, total, nmsg)
+    assert len(trials) >= 10 and all(t["ms"] > 0 for t in trials)
+    exp_enc, exp_off = oracle.encode_batch(data, off)
+    src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
+    for t in trials:
+        shape = dict(threads=t["threads"], tile=t["tile"], blocks_per_sm=t["blocks_per_sm"])
+        if kind == 2:
+            gb64.b64_shape_set(2, total, nmsg, **shape)
+        else:
+            gb64.b64_shape_set(3, int(exp_off[-1]), nmsg, **shape)
+        enc, eoff = gb64.b64_encode_batch(src, doff)
+        assert np.array_equal(enc.cpu().numpy()[:exp_enc.size], exp_enc)
+        dst, out_off, st, fb, ol = gb64.b64_decode_batch(enc, eoff)
+        assert int((st != 0).sum()) == 0
+        assert torch.equal(ol.cpu(), torch.from_numpy(np.diff(off)))
