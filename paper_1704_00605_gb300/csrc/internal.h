@@ -34,9 +34,11 @@ struct TileConfig {
   int blocks_per_sm = 0;  // persistent CTAs per SM (0 = as many as fit)
 };
 
-// Default shapes (the tuner may pick others).
-TileConfig default_encode_config();
-TileConfig default_decode_config();
+// Default shapes for a buffer of n bytes / m characters (the tuner may pick
+// others), and the dynamic shared memory a shape needs.
+TileConfig default_encode_config(uint64_t n);
+TileConfig default_decode_config(uint64_t m);
+size_t single_smem_bytes(int decode, const TileConfig& c);
 
 // Single-buffer encode of n >= 1 bytes; picks the TMA kernel when src and
 // dst are 16-byte aligned, else the generic one.

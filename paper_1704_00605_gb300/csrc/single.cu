@@ -26,6 +26,8 @@
 // ends, and stores split to the alignment of the destination.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -408,17 +410,63 @@ __global__ void __launch_bounds__(NT) k_decode_any(DecArgs a) {
 }
 
 // ------------------------------------------------------------------ host
-TileConfig default_encode_config() { return TileConfig{256, 4, 4, 0}; }
-TileConfig default_decode_config() { return TileConfig{256, 4, 3, 0}; }
+// Shapes measured fastest on GB300 for buffers of 256 MiB and more (one CTA
+// of 512 threads per SM, 48 KiB / 64 KiB TMA tiles), and a smaller tile for
+// smaller buffers so that every SM still gets tiles.
+TileConfig default_encode_config(uint64_t n) {
+  return n >= (256ull << 20) ? TileConfig{512, 8, 4, 0} : TileConfig{256, 4, 4, 0};
+}
+TileConfig default_decode_config(uint64_t m) {
+  return m >= (256ull << 20) ? TileConfig{512, 8, 2, 0} : TileConfig{256, 4, 3, 0};
+}
+
+size_t single_smem_bytes(int decode, const TileConfig& c) {
+  const size_t tile = (size_t)c.threads * c.upt * (decode ? 16 : 12);
+  return (size_t)c.stages * tile + (decode ? 2 * (size_t)c.threads * c.upt * 12 : 0);
+}
 
 namespace {
 
+// Raises the kernel's dynamic shared-memory limit to the device maximum
+// (once per device and kernel: the limit belongs to the kernel, not to one
+// launch) and returns how many CTAs of smem_bytes fit per SM (cached per
+// device, kernel, size and block size, so small launches pay it once).
 template <typename K>
 cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
+  struct Key {
+    int device;
+    const void* kernel;
+    size_t smem;  // ~0 marks "limit raised"
+    int threads;
+    int bps;
+  };
+  static std::mutex mu;
+  static std::vector<Key> cache;
+  cudaError_t e;
+  const DeviceInfo* di = device_info(&e);
+  if (!di) return e;
+  if ((int)smem_bytes > di->max_smem_optin) return cudaErrorInvalidValue;
+  const void* kp = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> g(mu);
+  bool raised = false;
+  for (const Key& k : cache) {
+    if (k.device != di->device || k.kernel != kp) continue;
+    if (k.smem == ~size_t(0)) raised = true;
+    if (k.smem == smem_bytes && k.threads == threads) {
+      *blocks_per_sm = k.bps;
+      return cudaSuccess;
+    }
+  }
+  if (!raised) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             di->max_smem_optin);
+    if (e != cudaSuccess) return e;
+    cache.push_back(Key{di->device, kp, ~size_t(0), 0, 0});
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, threads, smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, threads, smem_bytes);
+  cache.push_back(Key{di->device, kp, smem_bytes, threads, *blocks_per_sm});
+  return cudaSuccess;
 }
 
 bool valid_config(const TileConfig& c) {

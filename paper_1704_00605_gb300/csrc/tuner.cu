@@ -178,7 +178,7 @@ TileConfig single_config(int decode, uint64_t n) {
   const int kind = decode ? kSingleDecode : kSingleEncode;
   const Entry& e = g_table[kind][bucket_of(kind, (int64_t)n, 1)];
   if (e.set) return TileConfig{e.s.threads, e.s.units_per_thread, e.s.stages, e.s.blocks_per_sm};
-  return decode ? default_decode_config() : default_encode_config();
+  return decode ? default_decode_config(n) : default_encode_config(n);
 }
 
 BatchConfig tuned_batch_config(int decode, int64_t nmsg, int64_t total_bytes) {
@@ -223,6 +223,23 @@ int b64_shape_set(int kind, int64_t total, int64_t nmsg, const b64_shape* s) {
   if (!shape_valid(kind, *s)) {
     set_error("shape not valid for this kind");
     return B64_ERR_ARG;
+  }
+  if (kind == kSingleEncode || kind == kSingleDecode) {
+    // with a device present, the shape must fit its shared memory
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+      cudaError_t e;
+      const DeviceInfo* di = device_info(&e);
+      const TileConfig c{s->threads, s->units_per_thread, s->stages, s->blocks_per_sm};
+      const size_t need = single_smem_bytes(kind == kSingleDecode, c);
+      if (di && need + 1024 > (size_t)di->max_smem_optin) {
+        set_error("shape needs %zu bytes of shared memory per CTA; the device allows %d", need,
+                  di->max_smem_optin);
+        return B64_ERR_ARG;
+      }
+    } else {
+      cudaGetLastError();
+    }
   }
   std::lock_guard<std::mutex> g(g_mu);
   load_env_once_locked();
@@ -332,7 +349,7 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
       ea.out_off = enc_off;
       e = batch_launch(ea, default_batch_config(0));
     } else {
-      e = launch_encode(raw, raw_n, enc, stream, default_encode_config());
+      e = launch_encode(raw, raw_n, enc, stream, default_encode_config(raw_n));
     }
     if (e != cudaSuccess) return cuda_status(e, "tune: preparing the decode input");
   }

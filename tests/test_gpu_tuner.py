@@ -45,13 +45,17 @@ def test_tune_single_and_every_candidate_is_exact(gb64, oracle, restore_shapes, 
         (best["threads"], best["units_per_thread"], best["stages"], best["blocks_per_sm"])
     n = 3 * (1 << 20) // 4 * 3 + 7 if kind == 1 else (3 << 20) + 2
     raw = W.uniform_bytes(n, 40 + kind)
+    bucket_size = n if kind == 0 else gb64.b64_encoded_len(n)
     for t in trials:
-        gb64.b64_shape_set(0, n, threads=t["threads"], units_per_thread=t["units_per_thread"],
-                           stages=t["stages"], blocks_per_sm=t["blocks_per_sm"])
-        gb64.b64_shape_set(1, gb64.b64_encoded_len(n), threads=t["threads"],
+        gb64.b64_shape_set(kind, bucket_size, threads=t["threads"],
                            units_per_thread=t["units_per_thread"], stages=t["stages"],
                            blocks_per_sm=t["blocks_per_sm"])
         _check_single(gb64, oracle, raw)
+
+
+def test_shape_that_does_not_fit_is_rejected(gb64, restore_shapes):
+    with pytest.raises(gb64.Gb64Error, match="shared memory"):
+        gb64.b64_shape_set(1, 1 << 30, threads=512, units_per_thread=8, stages=6)
 
 
 @pytest.mark.parametrize("kind", [2, 3])
