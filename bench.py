@@ -48,11 +48,14 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=1200)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["large", "batched"], default="large")
+    p.add_argument("--config", choices=["large", "batched", "serve"], default="large")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched and serving sub-measurements of the default line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--small", action="store_true",
-                   help="192 MiB instead of 1 GiB (profiling captures); not a bench value")
+                   help="384 MiB instead of 1 GiB (profiling captures; same launch shapes as "
+                        "1 GiB); not a bench value")
     return p.parse_args(argv)
 
 
@@ -208,12 +211,12 @@ def traffic_from_profile(kernel_tag: str, src_hash: str):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the single-buffer kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1704_00605_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in ("common.cuh", "single.cu"):
+        h.update(name.encode())
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()
 
 
@@ -228,7 +231,7 @@ def run_large(args, d: Dist):
     pkg.build.ensure_built()
     g = pkg.load()
     dev = torch.device("cuda", d.local_rank)
-    base = (192 << 20) if args.small else GIB
+    base = (384 << 20) if args.small else GIB
     lengths = (base, base + 1, base + 2)
     data = W.uniform_bytes(base + 2, 1)  # the 1 GiB workload's stream (prefix when --small)
     src_all = torch.from_numpy(data).to(dev)
@@ -312,7 +315,7 @@ def run_large(args, d: Dist):
         "dtype": "u8",
         "data": "synthetic: uniform random bytes, numpy default_rng(1), 2^30+2 bytes",
         "config": {"workload": ("single large buffer: 1 GiB (+1, +2) encode + decode (config 2)"
-                                if not args.small else "192 MiB profiling case (not a bench value)"),
+                                if not args.small else "384 MiB profiling case (not a bench value)"),
                    "lengths": list(lengths), "encoded_chars": g.b64_encoded_len(base),
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{d.world}"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dominant}_tma", "achieved": round(dom_gbs, 1),
@@ -507,6 +510,69 @@ def batched_line(args, d: Dist):
     }
 
 
+# ------------------------------------------------------ serving workload
+def run_serve(args, d: Dist, duration_s: float):
+    """Config 5: Poisson arrivals at 200k requests/s, 50/50 encode/decode,
+    log-normal payloads (median 4 KiB, sigma 2, clipped to 1 B..16 MiB),
+    seed 4, replayed open-loop by native threads against the continuous
+    batching server with an 8 GiB memory budget. Payloads live in resident
+    device pools: a 1 GiB byte pool and its encoding (decode requests are
+    quad-aligned slices of it, 4*ceil(len/3) characters)."""
+    import torch
+
+    import paper_1704_00605_gb300 as pkg
+    from paper_1704_00605_gb300 import workloads as W
+
+    torch.cuda.set_device(d.local_rank)
+    g = pkg.load()
+    raw = W.counter_bytes_torch(4, 0, GIB, device=torch.device("cuda", d.local_rank))
+    enc = g.b64_encode(raw)
+    r = W.serving(duration_s=duration_s, rate_hz=200_000.0, seed=4)
+    n = r["t_arrival"].size
+    kind = r["is_decode"].astype(np.int32)
+    length = r["length"].astype(np.int64)
+    m = 4 * ((length + 2) // 3)
+    enc_pos = 4 * np.floor(r["pool_pos"] * ((enc.numel() - m) // 4)).astype(np.int64)
+    raw_pos = np.floor(r["pool_pos"] * (raw.numel() - length)).astype(np.int64)
+    src = np.where(kind == 1, enc.data_ptr() + enc_pos, raw.data_ptr() + raw_pos).astype(np.uint64)
+    ln = np.where(kind == 1, m, length)
+    with g.Server(memory_budget=8 << 30, streams=4, max_batch_msgs=8192,
+                  max_batch_bytes=512 << 20, auto_release=True) as srv:
+        t0 = time.perf_counter()
+        lat, st = srv.replay(r["t_arrival"] * 1e6, kind, src, ln)
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    ok = st == 0
+    lat_ok = lat[ok]
+    return {
+        "requests": int(n), "duration_s": duration_s, "offered_rps": 200_000.0,
+        "completed_rps": round(int(ok.sum()) / wall, 1),
+        "p50_us": round(float(np.percentile(lat_ok, 50)), 1),
+        "p99_us": round(float(np.percentile(lat_ok, 99)), 1),
+        "p999_us": round(float(np.percentile(lat_ok, 99.9)), 1),
+        "mean_us": round(float(lat_ok.mean()), 1),
+        "sustained_gbs": round(float(ln[ok].sum()) / wall / 1e9, 3),
+        "batches": stats["batches"], "mean_batch": round(stats["requests_launched"] /
+                                                         max(stats["batches"], 1), 1),
+        "memory_waits": stats["memory_waits"], "rejected": stats["rejected"],
+        "arena_high_water_bytes": stats["arena_high_water"], "memory_budget_bytes": 8 << 30,
+        "status_ok": int(ok.sum()),
+    }
+
+
+def serve_line(args, d: Dist):
+    s = run_serve(args, d, duration_s=30.0)
+    return {
+        "metric": "serving p99 latency (200k req/s Poisson, 50/50 encode/decode)",
+        "value": s["p99_us"], "unit": "us", "n_gpus": d.world, "steps": 1, "warmup": 0,
+        "ms_per_step": s["duration_s"] * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic: Poisson arrivals, log-normal payloads (median 4 KiB, sigma 2), seed 4",
+        "config": {"workload": "serving: 200k req/s for 30 s, 8 GiB admission budget (config 5)"},
+        "serve": s,
+    }
+
+
 # ------------------------------------------------------ reference arm
 def run_reference(args, d: Dist):
     """The CPU oracle as it stands, on the host cores, on bounded samples of
@@ -554,10 +620,13 @@ def main(argv=None):
     d = Dist()
     if args.config == "batched":
         line = batched_line(args, d)
+    elif args.config == "serve":
+        line = serve_line(args, d)
     else:
         line = run_large(args, d)
-        if not args.small:
+        if not args.small and not args.no_extras:
             line["batched"] = run_batched(args, d)
+            line["serve"] = run_serve(args, d, duration_s=3.0)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()

@@ -180,6 +180,74 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape *trials, int max_t
 int b64_tune_save(const char *path);
 int b64_tune_load(const char *path);
 
+/* ---- serving engine (no counterpart in the paper) ----------------------
+ * Continuous batching of encode/decode requests whose payloads are resident
+ * in device memory. An engine thread admits requests by device memory (all
+ * of a batch's buffers come from one arena of memory_budget bytes allocated
+ * at creation; a batch that does not fit waits for earlier outputs to be
+ * released), forms a batch per free stream slot from the requests that have
+ * arrived, packs their payloads with a gather kernel, runs the batched codec
+ * kernels, and reports completions. Requests that arrive while batches run
+ * join the next batch; batches on different slots overlap on the GPU. */
+typedef struct b64_server b64_server;
+
+typedef struct {
+  int64_t memory_budget;   /* bytes of device memory the server may hold */
+  int32_t streams;         /* batches in flight at once, 1..16 */
+  int32_t max_batch_msgs;  /* requests per batch, 1..65536 */
+  int64_t max_batch_bytes; /* payload bytes per batch (a larger request runs alone) */
+  int32_t auto_release;    /* 1: outputs are freed when polled (out is then invalid) */
+  int32_t reserved;
+} b64_server_config;
+
+typedef struct {
+  int64_t id;           /* from b64_server_submit */
+  int32_t kind;         /* 0 encode, 1 decode */
+  int32_t status;       /* b64_status of the request */
+  int64_t first_bad;    /* decode: as b64_decode; encode: -1 */
+  int64_t outlen;       /* bytes (decode) or characters (encode) produced */
+  const uint8_t *out;   /* device pointer to the output, valid until released */
+  int64_t len;          /* payload length */
+  int64_t batch;        /* batch sequence number */
+  double t_arrival_us;  /* server clock: arrival, admission, completion seen */
+  double t_admit_us;
+  double t_done_us;
+} b64_completion;
+
+typedef struct {
+  int64_t requests_submitted, requests_launched, requests_done, rejected;
+  int64_t batches, memory_waits;
+  int64_t arena_bytes, arena_in_use, arena_high_water, bytes_in;
+} b64_server_stats;
+
+/* Creates a server on the current device (allocates its arena and pinned
+ * staging, starts the engine thread). NULL on error (b64_last_error()). */
+b64_server *b64_server_create(const b64_server_config *cfg);
+/* Microseconds since the server was created (the clock of all timestamps). */
+double b64_server_now_us(b64_server *server);
+/* Queues one request: kind 0 encode / 1 decode of len bytes at src (device
+ * memory that must stay valid until the request completes). t_arrival_us < 0
+ * means now. Thread-safe. B64_ERR_NOMEM if one request alone exceeds the
+ * memory budget. */
+int b64_server_submit(b64_server *server, int kind, const uint8_t *src, int64_t len,
+                      double t_arrival_us, int64_t *id);
+/* Up to max completions (waiting up to timeout_us for the first); returns
+ * how many, or a negative b64_status. */
+int b64_server_poll(b64_server *server, b64_completion *out, int max, int timeout_us);
+/* Frees a completed request's output (its batch's memory is returned to
+ * the arena when every request of the batch is released). */
+int b64_server_release(b64_server *server, int64_t id);
+int b64_server_stats_get(b64_server *server, b64_server_stats *out);
+/* Open-loop replay from native threads: request i is submitted at
+ * t_arrival_us[i] after the call starts (kind[i], src[i] as a device address,
+ * len[i]); returns when all have completed, with latency_us[i] = completion
+ * minus scheduled arrival and status[i] (may be null). Needs auto_release. */
+int b64_server_replay(b64_server *server, int64_t n, const double *t_arrival_us,
+                      const int32_t *kind, const uint64_t *src, const int64_t *len,
+                      double *latency_us, int32_t *status);
+/* Stops the engine, waits for work in flight, frees everything. */
+void b64_server_destroy(b64_server *server);
+
 /* Human-readable name of a b64_status value (static string). */
 const char *b64_status_str(int status);
 

@@ -60,6 +60,7 @@ void clear_error() { t_error.clear(); }
 
 int cuda_status(cudaError_t e, const char* what) {
   set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  cudaGetLastError();  // do not leave a non-sticky error for the caller's next CUDA call
   return e == cudaErrorMemoryAllocation ? B64_ERR_NOMEM : B64_ERR_CUDA;
 }
 

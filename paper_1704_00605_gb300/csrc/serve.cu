@@ -1,0 +1,601 @@
+// Serving engine: continuous batching of encode and decode requests.
+//
+// Requests name a device-resident payload (pointer + length) and arrive at
+// any time (b64_server_submit, thread-safe). One engine thread
+//   - admits requests by device memory: every batch takes one block of a
+//     fixed arena (the memory budget) holding its offsets, results, scan
+//     scratch, packed inputs and outputs; a batch that does not fit waits
+//     until earlier batches are released (counted as a memory wait);
+//   - forms a batch per free stream slot from the pending requests of one
+//     kind (the kind whose oldest request is oldest), up to max_batch_msgs
+//     requests and max_batch_bytes input bytes, so requests that arrive while
+//     other batches run join the next batch (continuous batching);
+//   - launches on its slot's stream: one host-to-device copy of the offsets
+//     and gather descriptors, a gather kernel packing the payloads into the
+//     block, the batched codec kernels (batch.cu), one device-to-host copy of
+//     the per-message results, and an event; batches on different slots
+//     overlap on the device;
+//   - polls the events and turns finished batches into completions
+//     (status, first_bad, outlen, a device pointer to the output, and the
+//     arrival/admission/launch/completion times).
+// Outputs stay in the arena until the request is released.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch.h"
+#include "common.cuh"
+#include "internal.h"
+#include "tuner.h"
+
+namespace gb64 {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct GatherDesc {
+  const uint8_t* src;
+  int64_t len;
+  int64_t dst_off;
+};
+
+// Packs each request's payload into the batch's input region. CTA
+// (x, y) copies 16-byte units y, y + gridDim.y, ... of request x, x +
+// gridDim.x, ... (unaligned sources and destinations handled per unit).
+__global__ void k_gather(const GatherDesc* __restrict__ d, int64_t n, uint8_t* __restrict__ dst) {
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const GatherDesc g = d[j];
+    const uint8_t* s = g.src;
+    uint8_t* o = dst + g.dst_off;
+    const int64_t units = g.len / 16;
+    for (int64_t u = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.y * blockDim.x)
+      store16_any(o + 16 * u, load16_any(s + 16 * u, s, s + g.len));
+    if (blockIdx.y == 0)
+      for (int64_t i = 16 * units + threadIdx.x; i < g.len; i += blockDim.x) o[i] = s[i];
+  }
+}
+
+struct Arena {
+  uint8_t* base = nullptr;
+  uint64_t size = 0, used = 0, high_water = 0;
+  std::map<uint64_t, uint64_t> free_;  // offset -> bytes
+
+  static uint64_t round(uint64_t n) { return (n + 255) & ~255ull; }
+  void init(uint8_t* b, uint64_t n) {
+    base = b;
+    size = n;
+    free_.clear();
+    free_[0] = n;
+  }
+  bool alloc(uint64_t n, uint64_t* off) {
+    n = round(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const uint64_t o = it->first, rest = it->second - n;
+      free_.erase(it);
+      if (rest) free_[o + n] = rest;
+      *off = o;
+      used += n;
+      high_water = std::max(high_water, used);
+      return true;
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t n) {
+    n = round(n);
+    used -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct Request {
+  int kind = 0;
+  const uint8_t* src = nullptr;
+  int64_t len = 0;
+  double t_arrival = 0, t_admit = 0, t_launch = 0;
+  int64_t batch = -1;
+  int index = 0;  // position inside the batch
+  bool done = false, released = false;
+};
+
+// Block layout of one batch (offsets from the block start).
+struct Layout {
+  uint64_t in_off, desc, out_off, status, first_bad, outlen, scratch, in, out, total;
+  uint64_t h2d_bytes, d2h_bytes;
+};
+
+Layout layout_for(int64_t n, int64_t in_bytes, int64_t out_bytes) {
+  auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
+  Layout L;
+  L.in_off = 0;
+  L.desc = L.in_off + (uint64_t)(n + 1) * 8;
+  L.out_off = up(L.desc + (uint64_t)n * sizeof(GatherDesc));
+  L.status = L.out_off + (uint64_t)(n + 1) * 8;
+  L.first_bad = L.status + ((uint64_t)n * 4 + 7) / 8 * 8;
+  L.outlen = L.first_bad + (uint64_t)n * 8;
+  L.scratch = up(L.outlen + (uint64_t)n * 8);
+  L.in = up(L.scratch + batch_scratch_bytes(n));
+  L.out = up(L.in + (uint64_t)in_bytes + 16);
+  L.total = L.out + (uint64_t)out_bytes + 16;
+  L.h2d_bytes = L.desc + (uint64_t)n * sizeof(GatherDesc);
+  L.d2h_bytes = L.scratch - L.out_off;
+  return L;
+}
+
+struct Batch {
+  int kind = 0;
+  std::vector<int64_t> reqs;
+  uint64_t block = 0, block_bytes = 0;
+  Layout L{};
+  int slot = -1;
+  int unreleased = 0;
+  bool finished = false;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  uint8_t* host = nullptr;  // pinned: h2d staging then d2h results
+  uint64_t host_bytes = 0;
+  int64_t batch = -1;
+};
+
+}  // namespace
+}  // namespace gb64
+
+struct b64_server {
+  gb64::Arena arena;
+  b64_server_config cfg{};
+  int device = 0;
+  std::vector<gb64::Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<gb64::Request> reqs;  // index = request id (stable references)
+  std::deque<int64_t> pending[2];
+  std::map<int64_t, gb64::Batch> batches;
+  int64_t next_batch = 0;
+  std::deque<b64_completion> done_q;
+  b64_server_stats stats{};
+  std::atomic<bool> stop{false};
+  std::thread engine;
+  gb64::Clock::time_point t0;
+  int error = 0;
+  std::atomic<int64_t> inflight{0};
+
+  double now_us() const {
+    return std::chrono::duration<double, std::micro>(gb64::Clock::now() - t0).count();
+  }
+};
+
+namespace gb64 {
+namespace {
+
+int64_t out_capacity(int kind, int64_t len) {
+  return kind ? (int64_t)b64_decoded_cap((size_t)len) : (int64_t)b64_encoded_len((size_t)len);
+}
+
+void release_block_locked(b64_server* S, int64_t bid) {
+  auto it = S->batches.find(bid);
+  if (it == S->batches.end()) return;
+  S->arena.release(it->second.block, it->second.block_bytes);
+  S->batches.erase(it);
+}
+
+// Launches batch `bid` on its slot (lock held). Returns a CUDA error.
+cudaError_t launch_batch(b64_server* S, int64_t bid) {
+  Batch& B = S->batches[bid];
+  Slot& sl = S->slots[B.slot];
+  const int64_t n = (int64_t)B.reqs.size();
+  uint8_t* blk = S->arena.base + B.block;
+  // host staging: in_off then gather descriptors
+  int64_t* h_in_off = reinterpret_cast<int64_t*>(sl.host + B.L.in_off);
+  GatherDesc* h_desc = reinterpret_cast<GatherDesc*>(sl.host + B.L.desc);
+  h_in_off[0] = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const Request& r = S->reqs[B.reqs[j]];
+    h_desc[j] = GatherDesc{r.src, r.len, h_in_off[j]};
+    h_in_off[j + 1] = h_in_off[j] + r.len;
+  }
+  cudaError_t e = cudaMemcpyAsync(blk, sl.host, B.L.h2d_bytes, cudaMemcpyHostToDevice, sl.stream);
+  if (e != cudaSuccess) return e;
+  const int64_t in_bytes = h_in_off[n];
+  // large payloads spread their 16-byte units over more CTAs (grid.y)
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(64, in_bytes / n / (256 * 16 * 4) + 1));
+  k_gather<<<dim3((unsigned)std::min<int64_t>(n, 65535), (unsigned)gy), 256, 0, sl.stream>>>(
+      reinterpret_cast<const GatherDesc*>(blk + B.L.desc), n, blk + B.L.in);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  BatchArgs a;
+  a.decode = B.kind;
+  a.src = blk + B.L.in;
+  a.in_off = reinterpret_cast<const int64_t*>(blk + B.L.in_off);
+  a.nmsg = n;
+  a.dst = blk + B.L.out;
+  a.out_off = reinterpret_cast<int64_t*>(blk + B.L.out_off);
+  a.status = reinterpret_cast<int32_t*>(blk + B.L.status);
+  a.first_bad = reinterpret_cast<int64_t*>(blk + B.L.first_bad);
+  a.outlen = reinterpret_cast<int64_t*>(blk + B.L.outlen);
+  a.stream = sl.stream;
+  batch_scratch_split(blk + B.L.scratch, n, &a.tile_off, &a.parts);
+  e = batch_launch(a, tuned_batch_config(B.kind, n, in_bytes));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(sl.host + B.L.out_off, blk + B.L.out_off, B.L.d2h_bytes,
+                      cudaMemcpyDeviceToHost, sl.stream);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(sl.done, sl.stream);
+}
+
+// Tries to form and launch one batch on a free slot (lock held). Returns
+// true if a batch was launched.
+bool try_launch(b64_server* S) {
+  int slot = -1;
+  for (size_t i = 0; i < S->slots.size(); ++i)
+    if (S->slots[i].batch < 0) {
+      slot = (int)i;
+      break;
+    }
+  if (slot < 0) return false;
+  int kind = -1;
+  double oldest = 1e300;
+  for (int k = 0; k < 2; ++k)
+    if (!S->pending[k].empty() && S->reqs[S->pending[k].front()].t_arrival < oldest) {
+      oldest = S->reqs[S->pending[k].front()].t_arrival;
+      kind = k;
+    }
+  if (kind < 0) return false;
+  std::deque<int64_t>& q = S->pending[kind];
+  int64_t n = 0, in_bytes = 0, out_bytes = 0;
+  while (n < (int64_t)q.size() && n < S->cfg.max_batch_msgs) {
+    const Request& r = S->reqs[q[n]];
+    if (n > 0 && in_bytes + r.len > S->cfg.max_batch_bytes) break;
+    in_bytes += r.len;
+    out_bytes += out_capacity(kind, r.len);
+    ++n;
+  }
+  // admission by memory: shrink the batch until its block fits the arena
+  uint64_t off = 0;
+  Layout L{};
+  while (n > 0) {
+    in_bytes = out_bytes = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      in_bytes += S->reqs[q[j]].len;
+      out_bytes += out_capacity(kind, S->reqs[q[j]].len);
+    }
+    L = layout_for(n, in_bytes, out_bytes);
+    if (S->arena.alloc(L.total, &off)) break;
+    n = (n > 1) ? n / 2 : 0;
+  }
+  if (n == 0) {
+    S->stats.memory_waits++;
+    return false;
+  }
+  const int64_t bid = S->next_batch++;
+  Batch& B = S->batches[bid];
+  B.kind = kind;
+  B.block = off;
+  B.block_bytes = L.total;
+  B.L = L;
+  B.slot = slot;
+  B.unreleased = (int)n;
+  const double t = S->now_us();
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t id = q.front();
+    q.pop_front();
+    Request& r = S->reqs[id];
+    r.batch = bid;
+    r.index = (int)j;
+    r.t_admit = r.t_launch = t;
+    B.reqs.push_back(id);
+  }
+  S->slots[slot].batch = bid;
+  S->stats.batches++;
+  S->stats.requests_launched += n;
+  S->stats.bytes_in += in_bytes;
+  S->stats.arena_high_water = (int64_t)S->arena.high_water;
+  const cudaError_t e = launch_batch(S, bid);
+  if (e != cudaSuccess) {
+    S->error = cuda_status(e, "server: batch launch");
+    S->slots[slot].batch = -1;
+  }
+  return true;
+}
+
+// Moves finished batches to completions (lock held). Returns the number of
+// batches completed.
+int reap(b64_server* S) {
+  int nb = 0;
+  for (Slot& sl : S->slots) {
+    if (sl.batch < 0) continue;
+    const cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) {
+      S->error = cuda_status(q, "server: batch");
+    }
+    Batch& B = S->batches[sl.batch];
+    const double t = S->now_us();
+    const int64_t n = (int64_t)B.reqs.size();
+    const int64_t* out_off = reinterpret_cast<const int64_t*>(sl.host + B.L.out_off);
+    const int32_t* st = reinterpret_cast<const int32_t*>(sl.host + B.L.status);
+    const int64_t* fb = reinterpret_cast<const int64_t*>(sl.host + B.L.first_bad);
+    const int64_t* ol = reinterpret_cast<const int64_t*>(sl.host + B.L.outlen);
+    uint8_t* out = S->arena.base + B.block + B.L.out;
+    for (int64_t j = 0; j < n; ++j) {
+      Request& r = S->reqs[B.reqs[j]];
+      r.done = true;
+      b64_completion c{};
+      c.id = B.reqs[j];
+      c.kind = B.kind;
+      if (q != cudaSuccess) {
+        c.status = B64_ERR_CUDA;
+      } else if (B.kind) {
+        c.status = st[j];
+        c.first_bad = fb[j];
+        c.outlen = ol[j];
+      } else {
+        c.status = B64_OK;
+        c.first_bad = -1;
+        c.outlen = out_off[j + 1] - out_off[j];
+      }
+      c.out = out + out_off[j];
+      c.len = r.len;
+      c.t_arrival_us = r.t_arrival;
+      c.t_admit_us = r.t_admit;
+      c.t_done_us = t;
+      c.batch = sl.batch;
+      S->done_q.push_back(c);
+    }
+    B.finished = true;
+    sl.batch = -1;
+    S->stats.requests_done += n;
+    S->inflight -= n;
+    ++nb;
+  }
+  return nb;
+}
+
+void engine_main(b64_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (!S->stop) {
+    const int reaped = reap(S);
+    bool launched = false;
+    while (try_launch(S)) launched = true;
+    if (reaped) S->cv.notify_all();
+    bool busy = false;
+    for (const Slot& sl : S->slots) busy |= sl.batch >= 0;
+    if (!busy && S->pending[0].empty() && S->pending[1].empty()) {
+      S->cv.wait_for(lk, std::chrono::milliseconds(5));
+    } else if (!launched && !reaped) {
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gb64
+
+using namespace gb64;
+
+extern "C" {
+
+b64_server* b64_server_create(const b64_server_config* cfg_in) {
+  clear_error();
+  if (!cfg_in) {
+    set_error("config is null");
+    return nullptr;
+  }
+  b64_server_config cfg = *cfg_in;
+  if (cfg.memory_budget < (1 << 20) || cfg.streams < 1 || cfg.streams > 16 ||
+      cfg.max_batch_msgs < 1 || cfg.max_batch_msgs > 65536 || cfg.max_batch_bytes < 1) {
+    set_error("config out of range (budget >= 1 MiB, 1..16 streams, 1..65536 msgs per batch)");
+    return nullptr;
+  }
+  std::unique_ptr<b64_server> S(new b64_server());
+  S->cfg = cfg;
+  cudaError_t e = cudaGetDevice(&S->device);
+  uint8_t* mem = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&mem, (size_t)cfg.memory_budget);
+  if (e != cudaSuccess) {
+    cuda_status(e, "server: arena");
+    return nullptr;
+  }
+  S->arena.init(mem, (uint64_t)cfg.memory_budget);
+  S->stats.arena_bytes = cfg.memory_budget;
+  const uint64_t host_bytes = layout_for(cfg.max_batch_msgs, 0, 0).scratch;
+  S->slots.resize(cfg.streams);
+  for (Slot& sl : S->slots) {
+    e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl.host, host_bytes);
+    if (e != cudaSuccess) {
+      cuda_status(e, "server: streams");
+      return nullptr;
+    }
+    sl.host_bytes = host_bytes;
+  }
+  S->t0 = Clock::now();
+  b64_server* raw = S.release();
+  raw->engine = std::thread(engine_main, raw);
+  return raw;
+}
+
+double b64_server_now_us(b64_server* S) { return S ? S->now_us() : 0.0; }
+
+int b64_server_submit(b64_server* S, int kind, const uint8_t* src, int64_t len,
+                      double t_arrival_us, int64_t* id) {
+  clear_error();
+  if (!S || (kind != 0 && kind != 1) || len < 0 || (len > 0 && !src)) {
+    set_error("bad server, kind, length or source");
+    return B64_ERR_ARG;
+  }
+  const Layout L = layout_for(1, len, out_capacity(kind, len));
+  std::lock_guard<std::mutex> g(S->mu);
+  if (S->error) return S->error;
+  if (L.total > S->arena.size) {
+    S->stats.rejected++;
+    set_error("request of %lld bytes does not fit the memory budget", (long long)len);
+    return B64_ERR_NOMEM;
+  }
+  const int64_t rid = (int64_t)S->reqs.size();
+  Request r;
+  r.kind = kind;
+  r.src = src;
+  r.len = len;
+  r.t_arrival = t_arrival_us >= 0 ? t_arrival_us : S->now_us();
+  S->reqs.push_back(r);
+  S->pending[kind].push_back(rid);
+  S->stats.requests_submitted++;
+  S->inflight++;
+  if (id) *id = rid;
+  S->cv.notify_all();
+  return B64_OK;
+}
+
+static void release_locked(b64_server* S, int64_t id) {
+  Request& r = S->reqs[id];
+  if (r.released || !r.done) return;
+  r.released = true;
+  auto it = S->batches.find(r.batch);
+  if (it == S->batches.end()) return;
+  if (--it->second.unreleased == 0) release_block_locked(S, r.batch);
+}
+
+int b64_server_poll(b64_server* S, b64_completion* out, int max, int timeout_us) {
+  clear_error();
+  if (!S || (!out && max > 0)) return B64_ERR_ARG;
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->done_q.empty() && timeout_us > 0)
+    S->cv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return !S->done_q.empty(); });
+  int k = 0;
+  while (k < max && !S->done_q.empty()) {
+    out[k] = S->done_q.front();
+    S->done_q.pop_front();
+    if (S->cfg.auto_release) release_locked(S, out[k].id);
+    ++k;
+  }
+  if (S->error && k == 0) return S->error;
+  return k;
+}
+
+int b64_server_release(b64_server* S, int64_t id) {
+  clear_error();
+  if (!S) return B64_ERR_ARG;
+  std::lock_guard<std::mutex> g(S->mu);
+  if (id < 0 || id >= (int64_t)S->reqs.size() || !S->reqs[id].done) {
+    set_error("unknown or unfinished request");
+    return B64_ERR_ARG;
+  }
+  release_locked(S, id);
+  return B64_OK;
+}
+
+int b64_server_stats_get(b64_server* S, b64_server_stats* out) {
+  if (!S || !out) return B64_ERR_ARG;
+  std::lock_guard<std::mutex> g(S->mu);
+  *out = S->stats;
+  out->arena_in_use = (int64_t)S->arena.used;
+  return B64_OK;
+}
+
+int b64_server_replay(b64_server* S, int64_t n, const double* t_arrival_us, const int32_t* kind,
+                      const uint64_t* src, const int64_t* len, double* latency_us,
+                      int32_t* status) {
+  clear_error();
+  if (!S || n < 0 || (n > 0 && (!t_arrival_us || !kind || !src || !len || !latency_us))) {
+    set_error("bad replay arguments");
+    return B64_ERR_ARG;
+  }
+  if (!S->cfg.auto_release) {
+    set_error("replay needs a server created with auto_release");
+    return B64_ERR_ARG;
+  }
+  int64_t first = -1;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    first = (int64_t)S->reqs.size();
+  }
+  const double base = S->now_us();
+  std::atomic<int> submit_rc{B64_OK};
+  std::atomic<int64_t> accepted{0};
+  std::atomic<bool> submitted_all{false};
+  std::thread submitter([&] {
+    for (int64_t i = 0; i < n; ++i) {
+      const double target = base + t_arrival_us[i];
+      for (;;) {
+        const double dt = target - S->now_us();
+        if (dt <= 0) break;
+        if (dt > 300) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(dt - 200)));
+      }
+      int64_t id;
+      const int rc = b64_server_submit(S, kind[i], reinterpret_cast<const uint8_t*>(src[i]),
+                                       len[i], target, &id);
+      if (rc == B64_OK) {
+        accepted++;
+      } else {  // rejected (too large for the budget): never completes
+        submit_rc = rc;
+        latency_us[i] = -1;
+        if (status) status[i] = rc;
+      }
+    }
+    submitted_all = true;
+  });
+  std::vector<b64_completion> buf(4096);
+  int64_t got = 0;
+  int rc = B64_OK;
+  while (!(submitted_all && got >= accepted)) {
+    const int k = b64_server_poll(S, buf.data(), (int)buf.size(), 2000);
+    if (k < 0) {
+      rc = k;
+      break;
+    }
+    for (int j = 0; j < k; ++j) {
+      const int64_t i = buf[j].id - first;
+      if (i < 0 || i >= n) continue;
+      latency_us[i] = buf[j].t_done_us - buf[j].t_arrival_us;
+      if (status) status[i] = buf[j].status;
+      ++got;
+    }
+  }
+  submitter.join();
+  return rc != B64_OK ? rc : (int)submit_rc;
+}
+
+void b64_server_destroy(b64_server* S) {
+  if (!S) return;
+  S->stop = true;
+  S->cv.notify_all();
+  if (S->engine.joinable()) S->engine.join();
+  for (Slot& sl : S->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.host) cudaFreeHost(sl.host);
+  }
+  cudaFree(S->arena.base);
+  delete S;
+}
+
+}  // extern "C"

@@ -436,16 +436,15 @@ cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm
   struct Key {
     int device;
     const void* kernel;
-    size_t smem;  // ~0 marks "limit raised"
+    size_t smem;  // ~0 marks the entry recording the raised limit
     int threads;
-    int bps;
+    int bps;      // CTAs per SM, or the dynamic limit in the ~0 entry
   };
   static std::mutex mu;
   static std::vector<Key> cache;
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
-  if ((int)smem_bytes > di->max_smem_optin) return cudaErrorInvalidValue;
   const void* kp = reinterpret_cast<const void*>(kernel);
   std::lock_guard<std::mutex> g(mu);
   bool raised = false;
@@ -458,11 +457,19 @@ cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm
     }
   }
   if (!raised) {
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             di->max_smem_optin);
+    // dynamic + static shared memory of a CTA must stay within the opt-in limit
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
-    cache.push_back(Key{di->device, kp, ~size_t(0), 0, 0});
+    const int limit = di->max_smem_optin - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    if (e != cudaSuccess) return e;
+    cache.push_back(Key{di->device, kp, ~size_t(0), 0, limit});
   }
+  for (const Key& k : cache)
+    if (k.device == di->device && k.kernel == kp && k.smem == ~size_t(0) &&
+        (int)smem_bytes > k.bps)
+      return cudaErrorInvalidValue;  // the shape does not fit this device
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, threads, smem_bytes);
   if (e != cudaSuccess) return e;
   cache.push_back(Key{di->device, kp, smem_bytes, threads, *blocks_per_sm});

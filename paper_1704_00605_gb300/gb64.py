@@ -33,6 +33,32 @@ B64_KIND_ENCODE_BATCH = 2
 B64_KIND_DECODE_BATCH = 3
 
 
+class b64_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("streams", ctypes.c_int32),
+                ("max_batch_msgs", ctypes.c_int32), ("max_batch_bytes", ctypes.c_int64),
+                ("auto_release", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class b64_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("first_bad", ctypes.c_int64), ("outlen", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("len", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("t_arrival_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class b64_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "requests_submitted", "requests_launched", "requests_done", "rejected", "batches",
+        "memory_waits", "arena_bytes", "arena_in_use", "arena_high_water", "bytes_in")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class b64_shape(ctypes.Structure):
     """Launch shape (mirrors ``b64_shape`` in include/gb64.h)."""
 
@@ -84,6 +110,15 @@ def lib() -> ctypes.CDLL:
                            ctypes.POINTER(ctypes.c_int), vp]),
         "b64_tune_save": (i32, [ctypes.c_char_p]),
         "b64_tune_load": (i32, [ctypes.c_char_p]),
+        "b64_server_create": (vp, [ctypes.POINTER(b64_server_config)]),
+        "b64_server_now_us": (ctypes.c_double, [vp]),
+        "b64_server_submit": (i32, [vp, i32, vp, i64, ctypes.c_double, ctypes.POINTER(i64)]),
+        "b64_server_poll": (i32, [vp, ctypes.POINTER(b64_completion), i32, i32]),
+        "b64_server_release": (i32, [vp, i64]),
+        "b64_server_stats_get": (i32, [vp, ctypes.POINTER(b64_server_stats)]),
+        "b64_server_replay": (i32, [vp, i64, vp, vp, vp, vp, vp, vp]),
+        "b64_server_destroy": (None, [vp]),
+        "b64_decode_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -359,3 +394,91 @@ def b64_tune_save(path: str) -> None:
 def b64_tune_load(path: str) -> None:
     if lib().b64_tune_load(path.encode()) != B64_OK:
         raise Gb64Error(B64_ERR_ARG, b64_last_error())
+
+
+# ---------------------------------------------------------------- server
+def device_view(addr: int, n: int):
+    """A uint8 CUDA tensor viewing ``n`` bytes at device address ``addr``
+    (no copy; e.g. a completion's output, valid until it is released)."""
+    torch = _torch()
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (addr, False),
+                                    "version": 3, "strides": None}
+
+    return torch.as_tensor(_View(), device="cuda")
+
+
+
+class Server:
+    """Handle of a serving engine (``b64_server_create``); ``close()`` or the
+    context manager destroys it."""
+
+    def __init__(self, memory_budget=8 << 30, streams=4, max_batch_msgs=4096,
+                 max_batch_bytes=256 << 20, auto_release=False):
+        cfg = b64_server_config(memory_budget, streams, max_batch_msgs, max_batch_bytes,
+                                1 if auto_release else 0, 0)
+        h = lib().b64_server_create(ctypes.byref(cfg))
+        if not h:
+            raise Gb64Error(B64_ERR_ARG, b64_last_error())
+        self.h = ctypes.c_void_p(h)
+        self._keep = []
+
+    def now_us(self) -> float:
+        return float(lib().b64_server_now_us(self.h))
+
+    def submit(self, kind: int, src, length: int | None = None, t_arrival_us: float = -1.0) -> int:
+        """Queue a request on device memory ``src`` (tensor or address)."""
+        ptr = src if isinstance(src, int) else src.data_ptr()
+        n = length if length is not None else src.numel()
+        rid = ctypes.c_int64(-1)
+        st = lib().b64_server_submit(self.h, kind, ptr, n, t_arrival_us, ctypes.byref(rid))
+        if st != B64_OK:
+            raise Gb64Error(st, b64_last_error())
+        return int(rid.value)
+
+    def poll(self, max_items: int = 4096, timeout_us: int = 1000) -> list:
+        buf = (b64_completion * max_items)()
+        k = lib().b64_server_poll(self.h, buf, max_items, timeout_us)
+        if k < 0:
+            raise Gb64Error(k, b64_last_error())
+        return [buf[i].as_dict() for i in range(k)]
+
+    def release(self, rid: int) -> None:
+        st = lib().b64_server_release(self.h, rid)
+        if st != B64_OK:
+            raise Gb64Error(st, b64_last_error())
+
+    def stats(self) -> dict:
+        out = b64_server_stats()
+        lib().b64_server_stats_get(self.h, ctypes.byref(out))
+        return out.as_dict()
+
+    def replay(self, t_arrival_us, kind, src_ptrs, length):
+        """Open-loop replay from native threads; returns (latency_us, status)."""
+        t = np.ascontiguousarray(t_arrival_us, dtype=np.float64)
+        k = np.ascontiguousarray(kind, dtype=np.int32)
+        sp = np.ascontiguousarray(src_ptrs, dtype=np.uint64)
+        ln = np.ascontiguousarray(length, dtype=np.int64)
+        lat = np.full(t.size, -1.0)
+        st = np.zeros(t.size, dtype=np.int32)
+        rc = lib().b64_server_replay(self.h, t.size, t.ctypes.data, k.ctypes.data, sp.ctypes.data,
+                                     ln.ctypes.data, lat.ctypes.data, st.ctypes.data)
+        if rc != B64_OK:
+            raise Gb64Error(rc, b64_last_error())
+        return lat, st
+
+    def close(self):
+        if self.h:
+            lib().b64_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def b64_server_create(**cfg) -> Server:
+    return Server(**cfg)
