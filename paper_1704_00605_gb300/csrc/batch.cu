@@ -168,45 +168,67 @@ __device__ __forceinline__ int64_t owner_of(const int64_t* tile_off, int64_t nms
   return lo;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT)
-    k_batch_encode(const uint8_t* __restrict__ src, const int64_t* __restrict__ in_off,
-                   int64_t nmsg, uint8_t* __restrict__ dst, const int64_t* __restrict__ out_off,
-                   const int64_t* __restrict__ tile_off, int64_t tile) {
-  __shared__ uint8_t T[64];
-  init_tables(T, nullptr);
-  const int64_t total = tile_off[nmsg];
-  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-  int64_t t = (int64_t)blockIdx.x * per;
-  const int64_t t_end = min(total, t + per);
-  if (t >= t_end) return;
-  const uint8_t* src_lo = src;
-  const uint8_t* src_hi = src + in_off[nmsg];
-  int64_t j = owner_of(tile_off, nmsg, t);
-  const uint32_t tid = threadIdx.x;
-  for (; t < t_end; ++t) {
-    while (__ldg(tile_off + j + 1) <= t) ++j;
-    const int64_t k = t - __ldg(tile_off + j);
+// One message as a tile sees it: its bytes, its output, and the bounds that
+// aligned-word reads near its ends must stay within.
+struct Msg {
+  const uint8_t* src;
+  int64_t len;
+  uint8_t* out;
+  const uint8_t* lo;
+  const uint8_t* hi;
+};
+
+// Messages packed back to back in one buffer (the batched C ABI).
+struct PackedMsgs {
+  const uint8_t* src;
+  const int64_t* in_off;
+  uint8_t* dst;
+  const int64_t* out_off;
+  const uint8_t* src_hi;
+  __device__ __forceinline__ Msg get(int64_t j) const {
     const int64_t m0 = __ldg(in_off + j);
-    const int64_t mlen = __ldg(in_off + j + 1) - m0;
-    const int64_t t0 = k * tile;
-    const uint32_t len = (uint32_t)tmin<int64_t>(tile, mlen - t0);
-    const uint8_t* sp = src + m0 + t0;
-    uint8_t* dp = dst + __ldg(out_off + j) + t0 / 3 * 4;
-    const uint32_t nu = len / 12;
+    return Msg{src + m0, __ldg(in_off + j + 1) - m0, dst + __ldg(out_off + j), src, src_hi};
+  }
+  __device__ __forceinline__ int64_t len(int64_t j) const {
+    return __ldg(in_off + j + 1) - __ldg(in_off + j);
+  }
+  __device__ __forceinline__ void prepare(int64_t nmsg) { src_hi = src + __ldg(in_off + nmsg); }
+};
+
+// Messages anywhere in device memory, one descriptor each (the server).
+struct DescMsgs {
+  const MsgDesc* desc;
+  uint8_t* dst;
+  __device__ __forceinline__ Msg get(int64_t j) const {
+    const MsgDesc d = desc[j];
+    return Msg{d.src, d.len, dst + d.out_off, d.src, d.src + d.len};
+  }
+  __device__ __forceinline__ int64_t len(int64_t j) const { return desc[j].len; }
+  __device__ __forceinline__ void prepare(int64_t) {}
+};
+
+// Encodes tile [t0, t0 + tile) of message m (Algorithm 1 per unit; the
+// message's last tile also codes the partial group with its padding).
+template <int NT>
+__device__ __forceinline__ void encode_tile(const Msg& m, int64_t t0, int64_t tile,
+                                            const uint8_t* T) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t len = (uint32_t)tmin<int64_t>(tile, m.len - t0);
+  const uint8_t* sp = m.src + t0;
+  uint8_t* dp = m.out + t0 / 3 * 4;
+  const uint32_t nu = len / 12;
 #pragma unroll 2
-    for (uint32_t u = tid; u < nu; u += NT) {
-      const uint3 w = load12_any(sp + 12 * u, src_lo, src_hi);
-      store16_any(dp + 16 * u, enc_unit(w.x, w.y, w.z, T));
-    }
-    const uint32_t rest = len - 12 * nu;
-    const uint32_t ng = (rest + 2) / 3;
-    if (tid < ng) {
-      const uint8_t* p = sp + 12 * nu + 3 * tid;
-      const uint32_t cnt = min(3u, rest - 3 * tid);
-      const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
-      store4_any(dp + 16 * nu + 4 * tid, enc_tail_group(b0, b1, b2, cnt, T));
-    }
+  for (uint32_t u = tid; u < nu; u += NT) {
+    const uint3 w = load12_any(sp + 12 * u, m.lo, m.hi);
+    store16_any(dp + 16 * u, enc_unit(w.x, w.y, w.z, T));
+  }
+  const uint32_t rest = len - 12 * nu;
+  const uint32_t ng = (rest + 2) / 3;
+  if (tid < ng) {
+    const uint8_t* p = sp + 12 * nu + 3 * tid;
+    const uint32_t cnt = min(3u, rest - 3 * tid);
+    const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
+    store4_any(dp + 16 * nu + 4 * tid, enc_tail_group(b0, b1, b2, cnt, T));
   }
 }
 
@@ -246,11 +268,77 @@ __device__ uint32_t batch_dec_final(const uint8_t* src, uint64_t m, uint64_t bod
   return 0;
 }
 
+// Decodes tile [t0, t0 + tile) of message m (Algorithm 2 per unit; the tile
+// holding the message end also checks the final characters). Every thread
+// of the CTA must call it (warp-wide error reduction).
 template <int NT>
+__device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t tile,
+                                            const uint8_t* D, unsigned long long* fb,
+                                            int64_t* outlen_j) {
+  const uint32_t tid = threadIdx.x;
+  const uint64_t mlen = (uint64_t)m.len;
+  const uint64_t body_end = decode_body_end(mlen);
+  const uint32_t len = (uint32_t)tmin<uint64_t>(tile, mlen - t0);
+  const uint32_t body = body_end > t0 ? (uint32_t)tmin<uint64_t>(len, body_end - t0) : 0u;
+  const uint32_t nu = body / 16;
+  unsigned long long bad = ~0ull;
+#pragma unroll 2
+  for (uint32_t u = tid; u < nu; u += NT) {
+    const uint4 w = load16_any(m.src + t0 + 16 * u, m.lo, m.hi);
+    uint32_t err = 0;
+    store12_any(m.out + t0 / 4 * 3 + 12 * u, dec_unit(w, D, err));
+    if ((err & kBadFlag) && bad == ~0ull) bad = t0 + 16 * u + dec_unit_first_bad(w, D);
+  }
+  warp_min_to(fb, bad);
+  const uint32_t nq = (body - 16 * nu) / 4;
+  if (tid < nq) {
+    const uint64_t idx = t0 + 16 * nu + 4 * tid;
+    const uint8_t* p = m.src + idx;
+    const uint32_t x = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+                       ((uint32_t)p[3] << 24);
+    uint32_t err = 0;
+    const uint32_t v = dec_quad(x, D, err);
+    if (err & kBadFlag) {
+      for (uint32_t q = 0; q < 4; ++q)
+        if (D[(x >> (8 * q)) & 0xFFu] & kBadFlag) {
+          atomicMin(fb, (unsigned long long)(idx + q));
+          break;
+        }
+    } else {
+      uint8_t* o = m.out + idx / 4 * 3;
+      o[0] = (uint8_t)(v >> 16);
+      o[1] = (uint8_t)(v >> 8);
+      o[2] = (uint8_t)v;
+    }
+  }
+  if (tid == NT - 1 && body_end >= t0 && body_end < t0 + len)
+    *outlen_j = batch_dec_final(m.src, mlen, body_end, m.out, D, fb);
+}
+
+// Persistent tile walk: CTA b owns tiles [b*T/G, (b+1)*T/G) of the
+// T = tile_off[nmsg] tiles, in order.
+template <int NT, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_decode(const uint8_t* __restrict__ src, const int64_t* __restrict__ in_off,
-                   int64_t nmsg, uint8_t* __restrict__ dst, const int64_t* __restrict__ out_off,
-                   const int64_t* __restrict__ tile_off, int64_t tile,
+    k_batch_encode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile) {
+  __shared__ uint8_t T[64];
+  init_tables(T, nullptr);
+  const int64_t total = tile_off[nmsg];
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  int64_t t = (int64_t)blockIdx.x * per;
+  const int64_t t_end = min(total, t + per);
+  if (t >= t_end) return;
+  Msgs ms = msgs;
+  ms.prepare(nmsg);
+  int64_t j = owner_of(tile_off, nmsg, t);
+  for (; t < t_end; ++t) {
+    while (__ldg(tile_off + j + 1) <= t) ++j;
+    encode_tile<NT>(ms.get(j), (t - __ldg(tile_off + j)) * tile, tile, T);
+  }
+}
+
+template <int NT, class Msgs>
+__global__ void __launch_bounds__(NT)
+    k_batch_decode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
                    int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
   __shared__ uint8_t D[256];
   init_tables(nullptr, D);
@@ -259,65 +347,24 @@ __global__ void __launch_bounds__(NT)
   int64_t t = (int64_t)blockIdx.x * per;
   const int64_t t_end = min(total, t + per);
   if (t >= t_end) return;
-  const uint8_t* src_lo = src;
-  const uint8_t* src_hi = src + in_off[nmsg];
+  Msgs ms = msgs;
+  ms.prepare(nmsg);
   int64_t j = owner_of(tile_off, nmsg, t);
-  const uint32_t tid = threadIdx.x;
   for (; t < t_end; ++t) {
     while (__ldg(tile_off + j + 1) <= t) ++j;
-    const int64_t k = t - __ldg(tile_off + j);
-    const int64_t m0 = __ldg(in_off + j);
-    const uint64_t mlen = (uint64_t)(__ldg(in_off + j + 1) - m0);
-    const uint64_t body_end = decode_body_end(mlen);
-    const uint64_t t0 = (uint64_t)k * tile;
-    const uint32_t len = (uint32_t)tmin<uint64_t>(tile, mlen - t0);
-    const uint32_t body = body_end > t0 ? (uint32_t)tmin<uint64_t>(len, body_end - t0) : 0u;
-    const uint32_t nu = body / 16;
-    const uint8_t* mp = src + m0;
-    uint8_t* mo = dst + __ldg(out_off + j);
-    unsigned long long* fb = reinterpret_cast<unsigned long long*>(first_bad + j);
-    unsigned long long bad = ~0ull;
-#pragma unroll 2
-    for (uint32_t u = tid; u < nu; u += NT) {
-      const uint4 w = load16_any(mp + t0 + 16 * u, src_lo, src_hi);
-      uint32_t err = 0;
-      store12_any(mo + t0 / 4 * 3 + 12 * u, dec_unit(w, D, err));
-      if ((err & kBadFlag) && bad == ~0ull) bad = t0 + 16 * u + dec_unit_first_bad(w, D);
-    }
-    warp_min_to(fb, bad);
-    const uint32_t nq = (body - 16 * nu) / 4;
-    if (tid < nq) {
-      const uint64_t idx = t0 + 16 * nu + 4 * tid;
-      const uint8_t* p = mp + idx;
-      const uint32_t x = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
-                         ((uint32_t)p[3] << 24);
-      uint32_t err = 0;
-      const uint32_t v = dec_quad(x, D, err);
-      if (err & kBadFlag) {
-        for (uint32_t q = 0; q < 4; ++q)
-          if (D[(x >> (8 * q)) & 0xFFu] & kBadFlag) {
-            atomicMin(fb, (unsigned long long)(idx + q));
-            break;
-          }
-      } else {
-        uint8_t* o = mo + idx / 4 * 3;
-        o[0] = (uint8_t)(v >> 16);
-        o[1] = (uint8_t)(v >> 8);
-        o[2] = (uint8_t)v;
-      }
-    }
-    if (tid == NT - 1 && body_end >= t0 && body_end < t0 + len)
-      outlen[j] = batch_dec_final(mp, mlen, body_end, mo, D, fb);
+    decode_tile<NT>(ms.get(j), (uint64_t)(t - __ldg(tile_off + j)) * tile, tile, D,
+                    reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j);
   }
 }
 
-__global__ void k_batch_decode_finish(const int64_t* __restrict__ in_off, int64_t nmsg,
-                                      int32_t* __restrict__ status,
+// Per-message status: first bad character wins, then the length rule.
+template <class Msgs>
+__global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restrict__ status,
                                       int64_t* __restrict__ first_bad,
                                       int64_t* __restrict__ outlen) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nmsg) return;
-  const int64_t m = tmax<int64_t>(0, in_off[j + 1] - in_off[j]);
+  const int64_t m = max((long long)0, (long long)msgs.len(j));
   const int64_t fb = first_bad[j];
   if (fb != kNoBad) {
     status[j] = B64_ERR_INVALID_CHAR;
@@ -331,6 +378,15 @@ __global__ void k_batch_decode_finish(const int64_t* __restrict__ in_off, int64_
     first_bad[j] = m;
     outlen[j] = (int64_t)(decode_body_end((uint64_t)m) / 4 * 3) + outlen[j];
   }
+}
+
+// Initial per-message decode results for descriptor batches.
+__global__ void k_batch_decode_init(int64_t nmsg, int64_t* __restrict__ first_bad,
+                                    int64_t* __restrict__ outlen) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nmsg) return;
+  first_bad[j] = kNoBad;
+  outlen[j] = 0;
 }
 
 // ------------------------------------------------------------------ host
@@ -357,37 +413,69 @@ cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
 }
 
 namespace {
-template <int NT>
-cudaError_t launch_work(const BatchArgs& a, const BatchConfig& cfg, const DeviceInfo* di) {
+template <int NT, class Msgs>
+cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
+                        int32_t* status, int64_t* first_bad, int64_t* outlen,
+                        const BatchConfig& cfg, const DeviceInfo* di, cudaStream_t stream) {
   const int grid = di->sm_count * cfg.blocks_per_sm;
-  if (!a.decode) {
-    k_batch_encode<NT><<<grid, NT, 0, a.stream>>>(a.src, a.in_off, a.nmsg, a.dst, a.out_off,
-                                                  a.tile_off, cfg.tile);
-  } else {
-    k_batch_decode<NT><<<grid, NT, 0, a.stream>>>(a.src, a.in_off, a.nmsg, a.dst, a.out_off,
-                                                  a.tile_off, cfg.tile, a.first_bad, a.outlen);
+  if (!decode) {
+    k_batch_encode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile);
+    return cudaGetLastError();
   }
+  k_batch_decode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile, first_bad,
+                                                    outlen);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
+  k_batch_decode_finish<Msgs><<<(unsigned)blocks, 256, 0, stream>>>(msgs, nmsg, status, first_bad,
+                                                                   outlen);
   return cudaGetLastError();
 }
-}  // namespace
 
-cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
+template <class Msgs>
+cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
+                            int32_t* status, int64_t* first_bad, int64_t* outlen,
+                            const BatchConfig& cfg, cudaStream_t stream) {
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
-  e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, cfg.tile, a.parts,
-                    a.decode ? a.first_bad : nullptr, a.decode ? a.outlen : nullptr, a.stream);
-  if (e != cudaSuccess) return e;
   switch (cfg.threads) {
-    case 128: e = launch_work<128>(a, cfg, di); break;
-    case 512: e = launch_work<512>(a, cfg, di); break;
-    default: e = launch_work<256>(a, cfg, di); break;
+    case 128:
+      return launch_work<128>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
+                              stream);
+    case 512:
+      return launch_work<512>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
+                              stream);
+    default:
+      return launch_work<256>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
+                              stream);
   }
-  if (e != cudaSuccess || !a.decode) return e;
-  const int64_t blocks = std::max<int64_t>(1, (a.nmsg + 255) / 256);
-  k_batch_decode_finish<<<(unsigned)blocks, 256, 0, a.stream>>>(a.in_off, a.nmsg, a.status,
-                                                                a.first_bad, a.outlen);
-  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
+                              const int64_t* tile_off, int32_t* status, int64_t* first_bad,
+                              int64_t* outlen, const BatchConfig& cfg, bool init_results,
+                              cudaStream_t stream) {
+  if (decode && init_results) {
+    const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
+    k_batch_decode_init<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, first_bad, outlen);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, tile_off, status, first_bad, outlen,
+                         cfg, stream);
+}
+
+cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
+  cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, cfg.tile,
+                                a.parts, a.decode ? a.first_bad : nullptr,
+                                a.decode ? a.outlen : nullptr, a.stream);
+  if (e != cudaSuccess) return e;
+  // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
+  PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
+  return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen, cfg,
+                         a.stream);
 }
 
 int batch_read_and_clear_fault(unsigned int* out) {

@@ -31,6 +31,23 @@ struct BatchArgs {
   cudaStream_t stream = nullptr;
 };
 
+// One message of a descriptor batch: its bytes anywhere in device memory and
+// the offset of its output in the batch's output buffer.
+struct MsgDesc {
+  const uint8_t* src;
+  int64_t len;
+  int64_t out_off;
+};
+
+// Codes a batch described by host-built descriptors and tile offsets
+// (tile_off[j] = sum over earlier messages of ceil(len / cfg.tile)), with
+// no device scan: the persistent tile kernel (+ the decode finish kernel,
+// + an initialisation of first_bad/outlen when init_results).
+cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
+                              const int64_t* tile_off, int32_t* status, int64_t* first_bad,
+                              int64_t* outlen, const BatchConfig& cfg, bool init_results,
+                              cudaStream_t stream);
+
 // Bytes of scratch a batch of nmsg messages needs (tile_off + scan parts).
 size_t batch_scratch_bytes(int64_t nmsg);
 

@@ -3,25 +3,28 @@
 // Requests name a device-resident payload (pointer + length) and arrive at
 // any time (b64_server_submit, thread-safe). One engine thread
 //   - admits requests by device memory: every batch takes one block of a
-//     fixed arena (the memory budget) holding its offsets, results, scan
-//     scratch, packed inputs and outputs; a batch that does not fit waits
-//     until earlier batches are released (counted as a memory wait);
+//     fixed arena (the memory budget) for its descriptors, tile offsets,
+//     per-message results and outputs; a batch that does not fit waits until
+//     earlier outputs are released (counted as a memory wait);
 //   - forms a batch per free stream slot from the pending requests of one
 //     kind (the kind whose oldest request is oldest), up to max_batch_msgs
-//     requests and max_batch_bytes input bytes, so requests that arrive while
-//     other batches run join the next batch (continuous batching);
-//   - launches on its slot's stream: one host-to-device copy of the offsets
-//     and gather descriptors, a gather kernel packing the payloads into the
-//     block, the batched codec kernels (batch.cu), one device-to-host copy of
-//     the per-message results, and an event; batches on different slots
-//     overlap on the device;
+//     requests and max_batch_bytes payload bytes, so requests that arrive
+//     while other batches run join the next batch (continuous batching);
+//   - builds the batch's message descriptors and tile offsets on the host
+//     (from the request lengths; no device scan, no copy of the payloads),
+//     then, with the lock released, issues one host-to-device copy, the
+//     persistent batched codec kernel that reads each payload where it lives
+//     (plus the per-message finish kernel and one device-to-host copy of the
+//     results for decode) and an event; batches on different slots overlap
+//     on the device;
 //   - polls the events and turns finished batches into completions
 //     (status, first_bad, outlen, a device pointer to the output, and the
-//     arrival/admission/launch/completion times).
+//     arrival/admission/completion times).
 // Outputs stay in the arena until the request is released.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -32,7 +35,6 @@
 #include <vector>
 
 #include "batch.h"
-#include "common.cuh"
 #include "internal.h"
 #include "tuner.h"
 
@@ -40,29 +42,6 @@ namespace gb64 {
 namespace {
 
 using Clock = std::chrono::steady_clock;
-
-struct GatherDesc {
-  const uint8_t* src;
-  int64_t len;
-  int64_t dst_off;
-};
-
-// Packs each request's payload into the batch's input region. CTA
-// (x, y) copies 16-byte units y, y + gridDim.y, ... of request x, x +
-// gridDim.x, ... (unaligned sources and destinations handled per unit).
-__global__ void k_gather(const GatherDesc* __restrict__ d, int64_t n, uint8_t* __restrict__ dst) {
-  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
-    const GatherDesc g = d[j];
-    const uint8_t* s = g.src;
-    uint8_t* o = dst + g.dst_off;
-    const int64_t units = g.len / 16;
-    for (int64_t u = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; u < units;
-         u += (int64_t)gridDim.y * blockDim.x)
-      store16_any(o + 16 * u, load16_any(s + 16 * u, s, s + g.len));
-    if (blockIdx.y == 0)
-      for (int64_t i = 16 * units + threadIdx.x; i < g.len; i += blockDim.x) o[i] = s[i];
-  }
-}
 
 struct Arena {
   uint8_t* base = nullptr;
@@ -113,50 +92,55 @@ struct Request {
   int kind = 0;
   const uint8_t* src = nullptr;
   int64_t len = 0;
-  double t_arrival = 0, t_admit = 0, t_launch = 0;
+  double t_arrival = 0, t_admit = 0;
   int64_t batch = -1;
-  int index = 0;  // position inside the batch
   bool done = false, released = false;
 };
 
-// Block layout of one batch (offsets from the block start).
+// Block layout of one batch (offsets from the block start). The first
+// h2d_bytes are copied from the host; the d2h region holds decode results.
 struct Layout {
-  uint64_t in_off, desc, out_off, status, first_bad, outlen, scratch, in, out, total;
-  uint64_t h2d_bytes, d2h_bytes;
+  uint64_t desc, tile_off, first_bad, outlen, status, out, total;
+  uint64_t h2d_bytes, d2h_off, d2h_bytes;
 };
 
-Layout layout_for(int64_t n, int64_t in_bytes, int64_t out_bytes) {
+Layout layout_for(int64_t n, int64_t out_bytes, int kind) {
   auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
   Layout L;
-  L.in_off = 0;
-  L.desc = L.in_off + (uint64_t)(n + 1) * 8;
-  L.out_off = up(L.desc + (uint64_t)n * sizeof(GatherDesc));
-  L.status = L.out_off + (uint64_t)(n + 1) * 8;
-  L.first_bad = L.status + ((uint64_t)n * 4 + 7) / 8 * 8;
+  L.desc = 0;
+  L.tile_off = L.desc + (uint64_t)n * sizeof(MsgDesc);
+  L.first_bad = L.tile_off + (uint64_t)(n + 1) * 8;
   L.outlen = L.first_bad + (uint64_t)n * 8;
-  L.scratch = up(L.outlen + (uint64_t)n * 8);
-  L.in = up(L.scratch + batch_scratch_bytes(n));
-  L.out = up(L.in + (uint64_t)in_bytes + 16);
+  L.status = L.outlen + (uint64_t)n * 8;
+  L.out = up(L.status + (uint64_t)n * 4);
   L.total = L.out + (uint64_t)out_bytes + 16;
-  L.h2d_bytes = L.desc + (uint64_t)n * sizeof(GatherDesc);
-  L.d2h_bytes = L.scratch - L.out_off;
+  L.h2d_bytes = kind ? L.status : L.first_bad;
+  L.d2h_off = L.first_bad;
+  L.d2h_bytes = L.out - L.first_bad;
   return L;
 }
 
+struct Member {
+  int64_t id;
+  const uint8_t* src;
+  int64_t len;
+  int64_t out_off;
+};
+
 struct Batch {
   int kind = 0;
-  std::vector<int64_t> reqs;
+  std::vector<Member> members;
   uint64_t block = 0, block_bytes = 0;
   Layout L{};
+  BatchConfig cfg{};
   int slot = -1;
   int unreleased = 0;
-  bool finished = false;
 };
 
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  uint8_t* host = nullptr;  // pinned: h2d staging then d2h results
+  uint8_t* host = nullptr;  // pinned: staging of the h2d region, then the results
   uint64_t host_bytes = 0;
   int64_t batch = -1;
 };
@@ -181,7 +165,6 @@ struct b64_server {
   std::thread engine;
   gb64::Clock::time_point t0;
   int error = 0;
-  std::atomic<int64_t> inflight{0};
 
   double now_us() const {
     return std::chrono::duration<double, std::micro>(gb64::Clock::now() - t0).count();
@@ -202,60 +185,16 @@ void release_block_locked(b64_server* S, int64_t bid) {
   S->batches.erase(it);
 }
 
-// Launches batch `bid` on its slot (lock held). Returns a CUDA error.
-cudaError_t launch_batch(b64_server* S, int64_t bid) {
-  Batch& B = S->batches[bid];
-  Slot& sl = S->slots[B.slot];
-  const int64_t n = (int64_t)B.reqs.size();
-  uint8_t* blk = S->arena.base + B.block;
-  // host staging: in_off then gather descriptors
-  int64_t* h_in_off = reinterpret_cast<int64_t*>(sl.host + B.L.in_off);
-  GatherDesc* h_desc = reinterpret_cast<GatherDesc*>(sl.host + B.L.desc);
-  h_in_off[0] = 0;
-  for (int64_t j = 0; j < n; ++j) {
-    const Request& r = S->reqs[B.reqs[j]];
-    h_desc[j] = GatherDesc{r.src, r.len, h_in_off[j]};
-    h_in_off[j + 1] = h_in_off[j] + r.len;
-  }
-  cudaError_t e = cudaMemcpyAsync(blk, sl.host, B.L.h2d_bytes, cudaMemcpyHostToDevice, sl.stream);
-  if (e != cudaSuccess) return e;
-  const int64_t in_bytes = h_in_off[n];
-  // large payloads spread their 16-byte units over more CTAs (grid.y)
-  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(64, in_bytes / n / (256 * 16 * 4) + 1));
-  k_gather<<<dim3((unsigned)std::min<int64_t>(n, 65535), (unsigned)gy), 256, 0, sl.stream>>>(
-      reinterpret_cast<const GatherDesc*>(blk + B.L.desc), n, blk + B.L.in);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  BatchArgs a;
-  a.decode = B.kind;
-  a.src = blk + B.L.in;
-  a.in_off = reinterpret_cast<const int64_t*>(blk + B.L.in_off);
-  a.nmsg = n;
-  a.dst = blk + B.L.out;
-  a.out_off = reinterpret_cast<int64_t*>(blk + B.L.out_off);
-  a.status = reinterpret_cast<int32_t*>(blk + B.L.status);
-  a.first_bad = reinterpret_cast<int64_t*>(blk + B.L.first_bad);
-  a.outlen = reinterpret_cast<int64_t*>(blk + B.L.outlen);
-  a.stream = sl.stream;
-  batch_scratch_split(blk + B.L.scratch, n, &a.tile_off, &a.parts);
-  e = batch_launch(a, tuned_batch_config(B.kind, n, in_bytes));
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(sl.host + B.L.out_off, blk + B.L.out_off, B.L.d2h_bytes,
-                      cudaMemcpyDeviceToHost, sl.stream);
-  if (e != cudaSuccess) return e;
-  return cudaEventRecord(sl.done, sl.stream);
-}
-
-// Tries to form and launch one batch on a free slot (lock held). Returns
-// true if a batch was launched.
-bool try_launch(b64_server* S) {
+// Forms a batch for a free slot (lock held): pops its requests, allocates
+// its block, copies what the launch needs. Returns the batch id or -1.
+int64_t form_batch(b64_server* S) {
   int slot = -1;
   for (size_t i = 0; i < S->slots.size(); ++i)
     if (S->slots[i].batch < 0) {
       slot = (int)i;
       break;
     }
-  if (slot < 0) return false;
+  if (slot < 0) return -1;
   int kind = -1;
   double oldest = 1e300;
   for (int k = 0; k < 2; ++k)
@@ -263,32 +202,28 @@ bool try_launch(b64_server* S) {
       oldest = S->reqs[S->pending[k].front()].t_arrival;
       kind = k;
     }
-  if (kind < 0) return false;
+  if (kind < 0) return -1;
   std::deque<int64_t>& q = S->pending[kind];
-  int64_t n = 0, in_bytes = 0, out_bytes = 0;
+  int64_t n = 0, in_bytes = 0;
   while (n < (int64_t)q.size() && n < S->cfg.max_batch_msgs) {
-    const Request& r = S->reqs[q[n]];
-    if (n > 0 && in_bytes + r.len > S->cfg.max_batch_bytes) break;
-    in_bytes += r.len;
-    out_bytes += out_capacity(kind, r.len);
+    const int64_t len = S->reqs[q[n]].len;
+    if (n > 0 && in_bytes + len > S->cfg.max_batch_bytes) break;
+    in_bytes += len;
     ++n;
   }
   // admission by memory: shrink the batch until its block fits the arena
   uint64_t off = 0;
   Layout L{};
   while (n > 0) {
-    in_bytes = out_bytes = 0;
-    for (int64_t j = 0; j < n; ++j) {
-      in_bytes += S->reqs[q[j]].len;
-      out_bytes += out_capacity(kind, S->reqs[q[j]].len);
-    }
-    L = layout_for(n, in_bytes, out_bytes);
+    int64_t out_bytes = 0;
+    for (int64_t j = 0; j < n; ++j) out_bytes += out_capacity(kind, S->reqs[q[j]].len);
+    L = layout_for(n, out_bytes, kind);
     if (S->arena.alloc(L.total, &off)) break;
     n = (n > 1) ? n / 2 : 0;
   }
   if (n == 0) {
     S->stats.memory_waits++;
-    return false;
+    return -1;
   }
   const int64_t bid = S->next_batch++;
   Batch& B = S->batches[bid];
@@ -299,52 +234,86 @@ bool try_launch(b64_server* S) {
   B.slot = slot;
   B.unreleased = (int)n;
   const double t = S->now_us();
+  int64_t out_off = 0;
+  in_bytes = 0;
+  B.members.reserve(n);
   for (int64_t j = 0; j < n; ++j) {
     const int64_t id = q.front();
     q.pop_front();
     Request& r = S->reqs[id];
     r.batch = bid;
-    r.index = (int)j;
-    r.t_admit = r.t_launch = t;
-    B.reqs.push_back(id);
+    r.t_admit = t;
+    B.members.push_back(Member{id, r.src, r.len, out_off});
+    out_off += out_capacity(kind, r.len);
+    in_bytes += r.len;
   }
+  B.cfg = tuned_batch_config(kind, n, in_bytes);
   S->slots[slot].batch = bid;
   S->stats.batches++;
   S->stats.requests_launched += n;
   S->stats.bytes_in += in_bytes;
   S->stats.arena_high_water = (int64_t)S->arena.high_water;
-  const cudaError_t e = launch_batch(S, bid);
-  if (e != cudaSuccess) {
-    S->error = cuda_status(e, "server: batch launch");
-    S->slots[slot].batch = -1;
-  }
-  return true;
+  return bid;
 }
 
-// Moves finished batches to completions (lock held). Returns the number of
-// batches completed.
+// Stages and launches a formed batch (no lock needed: the batch and its
+// slot are owned by the engine thread until it is reaped).
+cudaError_t launch_batch(const Batch& B, Slot& sl, uint8_t* arena_base) {
+  const int64_t n = (int64_t)B.members.size();
+  uint8_t* blk = arena_base + B.block;
+  MsgDesc* h_desc = reinterpret_cast<MsgDesc*>(sl.host + B.L.desc);
+  int64_t* h_tile = reinterpret_cast<int64_t*>(sl.host + B.L.tile_off);
+  h_tile[0] = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const Member& m = B.members[j];
+    h_desc[j] = MsgDesc{m.src, m.len, m.out_off};
+    h_tile[j + 1] = h_tile[j] + (m.len + B.cfg.tile - 1) / B.cfg.tile;
+  }
+  if (B.kind) {
+    int64_t* h_fb = reinterpret_cast<int64_t*>(sl.host + B.L.first_bad);
+    int64_t* h_ol = reinterpret_cast<int64_t*>(sl.host + B.L.outlen);
+    for (int64_t j = 0; j < n; ++j) {
+      h_fb[j] = INT64_MAX;  // "no bad character yet"
+      h_ol[j] = 0;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(blk, sl.host, B.L.h2d_bytes, cudaMemcpyHostToDevice, sl.stream);
+  if (e != cudaSuccess) return e;
+  e = batch_launch_desc(B.kind, reinterpret_cast<const MsgDesc*>(blk + B.L.desc), n,
+                        blk + B.L.out, reinterpret_cast<const int64_t*>(blk + B.L.tile_off),
+                        reinterpret_cast<int32_t*>(blk + B.L.status),
+                        reinterpret_cast<int64_t*>(blk + B.L.first_bad),
+                        reinterpret_cast<int64_t*>(blk + B.L.outlen), B.cfg, false, sl.stream);
+  if (e != cudaSuccess) return e;
+  if (B.kind) {
+    e = cudaMemcpyAsync(sl.host + B.L.d2h_off, blk + B.L.d2h_off, B.L.d2h_bytes,
+                        cudaMemcpyDeviceToHost, sl.stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventRecord(sl.done, sl.stream);
+}
+
+// Moves finished batches to completions (lock held). Returns how many.
 int reap(b64_server* S) {
   int nb = 0;
   for (Slot& sl : S->slots) {
     if (sl.batch < 0) continue;
     const cudaError_t q = cudaEventQuery(sl.done);
     if (q == cudaErrorNotReady) continue;
-    if (q != cudaSuccess) {
-      S->error = cuda_status(q, "server: batch");
-    }
+    if (q != cudaSuccess) S->error = cuda_status(q, "server: batch");
     Batch& B = S->batches[sl.batch];
     const double t = S->now_us();
-    const int64_t n = (int64_t)B.reqs.size();
-    const int64_t* out_off = reinterpret_cast<const int64_t*>(sl.host + B.L.out_off);
+    const int64_t n = (int64_t)B.members.size();
     const int32_t* st = reinterpret_cast<const int32_t*>(sl.host + B.L.status);
     const int64_t* fb = reinterpret_cast<const int64_t*>(sl.host + B.L.first_bad);
     const int64_t* ol = reinterpret_cast<const int64_t*>(sl.host + B.L.outlen);
     uint8_t* out = S->arena.base + B.block + B.L.out;
     for (int64_t j = 0; j < n; ++j) {
-      Request& r = S->reqs[B.reqs[j]];
+      const Member& m = B.members[j];
+      Request& r = S->reqs[m.id];
       r.done = true;
       b64_completion c{};
-      c.id = B.reqs[j];
+      c.id = m.id;
       c.kind = B.kind;
       if (q != cudaSuccess) {
         c.status = B64_ERR_CUDA;
@@ -355,20 +324,18 @@ int reap(b64_server* S) {
       } else {
         c.status = B64_OK;
         c.first_bad = -1;
-        c.outlen = out_off[j + 1] - out_off[j];
+        c.outlen = out_capacity(0, m.len);
       }
-      c.out = out + out_off[j];
-      c.len = r.len;
+      c.out = out + m.out_off;
+      c.len = m.len;
+      c.batch = sl.batch;
       c.t_arrival_us = r.t_arrival;
       c.t_admit_us = r.t_admit;
       c.t_done_us = t;
-      c.batch = sl.batch;
       S->done_q.push_back(c);
     }
-    B.finished = true;
     sl.batch = -1;
     S->stats.requests_done += n;
-    S->inflight -= n;
     ++nb;
   }
   return nb;
@@ -379,14 +346,23 @@ void engine_main(b64_server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   while (!S->stop) {
     const int reaped = reap(S);
-    bool launched = false;
-    while (try_launch(S)) launched = true;
     if (reaped) S->cv.notify_all();
+    const int64_t bid = form_batch(S);
+    if (bid >= 0) {
+      Batch& B = S->batches[bid];  // std::map: stable while the lock is dropped
+      Slot& sl = S->slots[B.slot];
+      uint8_t* base = S->arena.base;
+      lk.unlock();
+      const cudaError_t e = launch_batch(B, sl, base);
+      lk.lock();
+      if (e != cudaSuccess) S->error = cuda_status(e, "server: batch launch");
+      continue;
+    }
     bool busy = false;
     for (const Slot& sl : S->slots) busy |= sl.batch >= 0;
     if (!busy && S->pending[0].empty() && S->pending[1].empty()) {
       S->cv.wait_for(lk, std::chrono::milliseconds(5));
-    } else if (!launched && !reaped) {
+    } else if (!reaped) {
       lk.unlock();
       std::this_thread::yield();
       lk.lock();
@@ -424,7 +400,7 @@ b64_server* b64_server_create(const b64_server_config* cfg_in) {
   }
   S->arena.init(mem, (uint64_t)cfg.memory_budget);
   S->stats.arena_bytes = cfg.memory_budget;
-  const uint64_t host_bytes = layout_for(cfg.max_batch_msgs, 0, 0).scratch;
+  const uint64_t host_bytes = layout_for(cfg.max_batch_msgs, 0, 1).out;
   S->slots.resize(cfg.streams);
   for (Slot& sl : S->slots) {
     e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
@@ -451,7 +427,7 @@ int b64_server_submit(b64_server* S, int kind, const uint8_t* src, int64_t len,
     set_error("bad server, kind, length or source");
     return B64_ERR_ARG;
   }
-  const Layout L = layout_for(1, len, out_capacity(kind, len));
+  const Layout L = layout_for(1, out_capacity(kind, len), kind);
   std::lock_guard<std::mutex> g(S->mu);
   if (S->error) return S->error;
   if (L.total > S->arena.size) {
@@ -468,7 +444,6 @@ int b64_server_submit(b64_server* S, int kind, const uint8_t* src, int64_t len,
   S->reqs.push_back(r);
   S->pending[kind].push_back(rid);
   S->stats.requests_submitted++;
-  S->inflight++;
   if (id) *id = rid;
   S->cv.notify_all();
   return B64_OK;
