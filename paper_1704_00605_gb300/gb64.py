@@ -206,6 +206,8 @@ def b64_decode(src, dst=None, stream=None):
     if dst is None:
         dst = torch.empty(max(cap, 1), dtype=torch.uint8, device=src.device)
     _check_u8(dst, "dst")
+    if dst.numel() < cap:
+        raise ValueError(f"dst holds {dst.numel()} bytes; decoding may write {cap}")
     outlen = ctypes.c_size_t(0)
     first_bad = ctypes.c_size_t(0)
     with torch.cuda.device(src.device):
@@ -255,6 +257,8 @@ def b64_encode_host(h_src, h_dst=None, stream=None):
     src = _host_u8(h_src)
     m = b64_encoded_len(src.size)
     dst = np.empty(max(m, 1), dtype=np.uint8) if h_dst is None else _host_u8(h_dst)
+    if dst.size < m:
+        raise ValueError(f"h_dst holds {dst.size} bytes; the encoding needs {m}")
     r = lib().b64_encode_host(src.ctypes.data if src.size else 0, src.size, dst.ctypes.data,
                               _stream(stream, torch.cuda.current_device()))
     if r == SIZE_MAX:
@@ -268,6 +272,8 @@ def b64_decode_host(h_src, h_dst=None, stream=None):
     src = _host_u8(h_src)
     cap = b64_decoded_cap(src.size)
     dst = np.empty(max(cap, 1), dtype=np.uint8) if h_dst is None else _host_u8(h_dst)
+    if dst.size < cap:
+        raise ValueError(f"h_dst holds {dst.size} bytes; decoding may write {cap}")
     outlen = ctypes.c_size_t(0)
     first_bad = ctypes.c_size_t(0)
     st = lib().b64_decode_host(src.ctypes.data if src.size else 0, src.size, dst.ctypes.data,
