@@ -26,6 +26,10 @@ _LIB = os.path.join(_HERE, "liboracle_b64.so")
 OK = 0
 INVALID_CHAR = 1
 BAD_LENGTH = 2
+NONCANONICAL = 3
+FLAG_URL = 1
+FLAG_NOPAD = 2
+FLAG_STRICT_TAIL = 4
 
 _lock = threading.Lock()
 _lib = None
@@ -67,6 +71,15 @@ def _load():
         lib.oracle_encode_batch.restype = None
         lib.oracle_decode_batch.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp]
         lib.oracle_decode_batch.restype = None
+        lib.oracle_encoded_len_ex.argtypes = [c_size, ctypes.c_int]
+        lib.oracle_encoded_len_ex.restype = c_size
+        lib.oracle_decoded_cap_ex.argtypes = [c_size, ctypes.c_int]
+        lib.oracle_decoded_cap_ex.restype = c_size
+        lib.oracle_encode_ex.argtypes = [vp, c_size, vp, ctypes.c_int]
+        lib.oracle_encode_ex.restype = c_size
+        lib.oracle_decode_ex.argtypes = [vp, c_size, vp, ctypes.POINTER(c_size),
+                                         ctypes.POINTER(c_size), ctypes.c_int]
+        lib.oracle_decode_ex.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -157,3 +170,23 @@ def decode_batch(src, in_off):
                                 out_off.ctypes.data, status.ctypes.data,
                                 first_bad.ctypes.data, outlen.ctypes.data)
     return dst[:cap], out_off, status, first_bad, outlen
+
+
+def encode_ex(data, flags: int) -> np.ndarray:
+    """Algorithm 1 with the base64url / no-padding variants of Section 2."""
+    src = _u8(data)
+    out = np.empty(max(int(_load().oracle_encoded_len_ex(src.size, flags)), 1), dtype=np.uint8)
+    k = _load().oracle_encode_ex(_ptr(src), src.size, out.ctypes.data, flags)
+    return out[:k].copy()
+
+
+def decode_ex(chars, flags: int):
+    """Strict Algorithm 2 with the Section 2 variants and Appendix A's check.
+    Returns ``(status, output_bytes, first_bad)``."""
+    src = _u8(chars)
+    out = np.empty(max(int(_load().oracle_decoded_cap_ex(src.size, flags)), 1), dtype=np.uint8)
+    outlen = ctypes.c_size_t(0)
+    first_bad = ctypes.c_size_t(0)
+    st = _load().oracle_decode_ex(_ptr(src), src.size, out.ctypes.data, ctypes.byref(outlen),
+                                  ctypes.byref(first_bad), flags)
+    return int(st), out[: outlen.value].copy(), int(first_bad.value)

@@ -180,3 +180,146 @@ void oracle_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg,
     outlen[j] = (int64_t)ol;
   }
 }
+
+/* ------------------------------------------------------------------------
+ * Variants (Section 2 and Appendix A), selected by flags:
+ *   ORACLE_FLAG_URL          base64url: value 62 is '-' and value 63 is '_'
+ *                            instead of '+' and '/' (Section 2).
+ *   ORACLE_FLAG_NOPAD        padding omitted (Section 2: acceptable when the
+ *                            size of the data is otherwise known): encode
+ *                            writes no '='; decode also accepts a final group
+ *                            of 2 or 3 characters (1 or 2 bytes). A final
+ *                            group of 1 character is still BAD_LENGTH.
+ *   ORACLE_FLAG_STRICT_TAIL  Appendix A: with two padding characters (or a
+ *                            2-character final group) (A(c) * 16) mod 256 = 0
+ *                            for the last data character c; with one (or a
+ *                            3-character final group) (A(c) * 64) mod 256 =
+ *                            0. A violation is status NONCANONICAL with
+ *                            first_bad = the index of c.
+ * With flags = 0 these functions compute exactly oracle_encode and
+ * oracle_decode (checked by the tests).
+ * ---------------------------------------------------------------------- */
+#define ORACLE_FLAG_URL 1
+#define ORACLE_FLAG_NOPAD 2
+#define ORACLE_FLAG_STRICT_TAIL 4
+#define ORACLE_NONCANONICAL 3
+
+/* B and A of the selected alphabet. */
+static char B_ex(unsigned v, int flags) {
+  if (flags & ORACLE_FLAG_URL) {
+    if (v == 62) return '-';
+    if (v == 63) return '_';
+  }
+  return B(v);
+}
+
+static int A_ex(unsigned char x, int flags) {
+  if (flags & ORACLE_FLAG_URL) {
+    if (x == '-') return 62;
+    if (x == '_') return 63;
+    if (x == '+' || x == '/') return -1;
+  }
+  return A(x);
+}
+
+size_t oracle_encoded_len_ex(size_t n, int flags) {
+  if (flags & ORACLE_FLAG_NOPAD) return 4 * (n / 3) + (n % 3 ? n % 3 + 1 : 0);
+  return oracle_encoded_len(n);
+}
+
+/* Algorithm 1 with the alphabet of `flags`; under NOPAD the padding
+ * characters are not appended. */
+size_t oracle_encode_ex(const uint8_t *s, size_t n, char *p, int flags) {
+  const int pad = !(flags & ORACLE_FLAG_NOPAD);
+  size_t k = 0;
+  size_t i;
+  for (i = 0; i + 3 <= n - (n % 3); i += 3) {
+    p[k++] = B_ex(s[i] / 4, flags);
+    p[k++] = B_ex(((s[i] * 16) % 64) + (s[i + 1] / 16), flags);
+    p[k++] = B_ex(((s[i + 1] * 4) % 64) + (s[i + 2] / 64), flags);
+    p[k++] = B_ex(s[i + 2] % 64, flags);
+  }
+  i = n - n % 3;
+  if (i < n) {
+    p[k++] = B_ex(s[i] / 4, flags);
+    if (i == n - 1) {
+      p[k++] = B_ex((s[i] * 16) % 64, flags);
+      if (pad) p[k++] = PAD;
+    } else if (i == n - 2) {
+      p[k++] = B_ex(((s[i] * 16) % 64) + (s[i + 1] / 16), flags);
+      p[k++] = B_ex((s[i + 1] * 4) % 64, flags);
+    }
+    if (pad) p[k++] = PAD;
+  }
+  return k;
+}
+
+size_t oracle_decoded_cap_ex(size_t m, int flags) {
+  size_t cap = 3 * (m / 4);
+  if ((flags & ORACLE_FLAG_NOPAD) && m % 4 >= 2) cap += m % 4 - 1;
+  return cap;
+}
+
+/* Algorithm 2 with readings R1-R4, the alphabet of `flags`, optional
+ * padding (NOPAD) and Appendix A's check (STRICT_TAIL). */
+int oracle_decode_ex(const char *c, size_t m, uint8_t *p, size_t *outlen, size_t *first_bad,
+                     int flags) {
+  const int nopad = (flags & ORACLE_FLAG_NOPAD) != 0;
+  size_t npad = padding_count(c, m);
+  for (size_t i = 0; i < m; i++) {
+    int is_padding = (npad > 0) && (i >= m - npad);
+    if (A_ex((unsigned char)c[i], flags) < 0 && !is_padding) {
+      *first_bad = i;
+      *outlen = 0;
+      return ORACLE_INVALID_CHAR;
+    }
+  }
+  if (m % 4 != 0 && (!nopad || m % 4 == 1)) {
+    *first_bad = m - m % 4;
+    *outlen = 0;
+    return ORACLE_BAD_LENGTH;
+  }
+  /* Appendix A on the last data character (padded or unpadded tail) */
+  if (flags & ORACLE_FLAG_STRICT_TAIL) {
+    size_t rest = nopad ? m % 4 : 0; /* characters of an unpadded final group */
+    size_t idx = 0;
+    int mult = 0;
+    if (npad == 2 || rest == 2) {
+      idx = (npad == 2) ? m - 3 : m - 1;
+      mult = 16;
+    } else if (npad == 1 || rest == 3) {
+      idx = (npad == 1) ? m - 2 : m - 1;
+      mult = 64;
+    }
+    if (mult && (A_ex((unsigned char)c[idx], flags) * mult) % 256 != 0) {
+      *first_bad = idx;
+      *outlen = 0;
+      return ORACLE_NONCANONICAL;
+    }
+  }
+  size_t k = 0;
+  const size_t whole = m - m % 4;
+  for (size_t i = 0; i + 4 <= whole; i += 4) {
+    int a = A_ex((unsigned char)c[i], flags);
+    int b = A_ex((unsigned char)c[i + 1], flags);
+    int cc = (c[i + 2] == PAD) ? 0 : A_ex((unsigned char)c[i + 2], flags);
+    int d = (c[i + 3] == PAD) ? 0 : A_ex((unsigned char)c[i + 3], flags);
+    p[k++] = (uint8_t)((a * 4) + (b / 16));
+    if (c[i + 2] == PAD) break;
+    p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 4));
+    if (c[i + 3] == PAD) break;
+    p[k++] = (uint8_t)(((cc * 64) % 256) + d);
+  }
+  if (m % 4 >= 2) { /* unpadded final group (NOPAD) */
+    int a = A_ex((unsigned char)c[whole], flags);
+    int b = A_ex((unsigned char)c[whole + 1], flags);
+    p[k++] = (uint8_t)((a * 4) + (b / 16));
+    if (m % 4 == 3) {
+      int cc = A_ex((unsigned char)c[whole + 2], flags);
+      p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 4));
+    }
+  }
+  *outlen = k;
+  *first_bad = m;
+  return ORACLE_OK;
+}

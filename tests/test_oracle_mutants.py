@@ -19,6 +19,18 @@ from tests import golden
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "oracle", "b64_oracle.c")
+VARIANTS_MARK = "/* ------------------------------------------------------------------------\n * Variants"
+
+
+def mutate(text: str, old: str, new: str, variants: bool) -> str:
+    """Replace the single occurrence of `old` in the base functions (or, with
+    variants=True, in the variant functions) of the oracle source."""
+    cut = text.index(VARIANTS_MARK)
+    head, tail = text[:cut], text[cut:]
+    region = tail if variants else head
+    assert region.count(old) == 1, f"mutation anchor not found exactly once: {old!r}"
+    region = region.replace(old, new)
+    return head + region if variants else region + tail
 
 MUTANTS = {
     "enc_drop_hi_term": ("B(((s[i] * 16) % 64) + (s[i + 1] / 16));\n    p[k++] = B(((s[i + 1]",
@@ -114,7 +126,81 @@ def test_unmodified_oracle_passes(tmp_path):
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
-    text = open(SRC).read()
-    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
-    lib = _compile(tmp_path, name, text.replace(old, new))
+    lib = _compile(tmp_path, name, mutate(open(SRC).read(), old, new, variants=False))
     assert not _pins_pass(lib), f"planted mistake {name} survived the pins"
+
+
+# --------------------------------------------------- the variant functions
+VARIANT_MUTANTS = {
+    "url_swap_62_63": ("if (v == 62) return '-';", "if (v == 63) return '-';"),
+    "url_accepts_plus_slash": ("    if (x == '+' || x == '/') return -1;\n", "\n"),
+    "strict_tail_wrong_multiplier": ("      mult = 16;", "      mult = 32;"),
+    "strict_tail_wrong_index": ("idx = (npad == 1) ? m - 2 : m - 1;", "idx = (npad == 1) ? m - 3 : m - 1;"),
+    "nopad_length_rule": ("if (m % 4 != 0 && (!nopad || m % 4 == 1)) {", "if (m % 4 != 0 && !nopad) {"),
+    "nopad_keeps_padding": ("      if (pad) p[k++] = PAD;\n    } else if", "      p[k++] = PAD;\n    } else if"),
+    "nopad_tail_shift": ("      p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 4));\n    }\n  }",
+                         "      p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 8));\n    }\n  }"),
+}
+
+
+def _bind_ex(lib):
+    lib.oracle_encode_ex.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int]
+    lib.oracle_encode_ex.restype = ctypes.c_size_t
+    lib.oracle_decode_ex.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.c_int]
+    lib.oracle_decode_ex.restype = ctypes.c_int
+    return lib
+
+
+def _enc_ex(lib, raw: bytes, flags: int) -> bytes:
+    out = ctypes.create_string_buffer(4 * (len(raw) // 3 + 1) + 4)
+    k = lib.oracle_encode_ex(raw, len(raw), out, flags)
+    return out.raw[:k]
+
+
+def _dec_ex(lib, s: bytes, flags: int):
+    out = ctypes.create_string_buffer(3 * (len(s) // 4) + 8)
+    ol, fb = ctypes.c_size_t(), ctypes.c_size_t()
+    st = lib.oracle_decode_ex(s, len(s), out, ctypes.byref(ol), ctypes.byref(fb), flags)
+    return st, out.raw[:ol.value], fb.value
+
+
+def _variant_pins_pass(lib) -> bool:
+    rng = np.random.default_rng(8)
+    for n in (0, 1, 2, 3, 4, 5, 62, 63, 64, 700):
+        raw = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        for flags, py in ((1, base64.urlsafe_b64encode(raw)), (2, base64.b64encode(raw).rstrip(b"=")),
+                          (3, base64.urlsafe_b64encode(raw).rstrip(b"="))):
+            if _enc_ex(lib, raw, flags) != py:
+                return False
+            st, out, fb = _dec_ex(lib, py, flags)
+            if st != 0 or out != raw:
+                return False
+    if _dec_ex(lib, b"ab+c", 1)[0] != 1:  # '+' is outside the url alphabet
+        return False
+    if _dec_ex(lib, b"QUJDQ", 2)[0::2] != (2, 4):  # one character past whole groups
+        return False
+    canon1 = {base64.b64encode(bytes([a])) for a in range(256)}
+    canon2 = {base64.b64encode(bytes([a, b])) for a in range(256) for b in range(0, 256, 7)}
+    for s in canon1:
+        if _dec_ex(lib, s, 4)[0] != 0:
+            return False
+    for s in canon2:
+        if _dec_ex(lib, s, 4)[0] != 0:
+            return False
+    for s, fb in ((b"QR==", 1), (b"QI==", 1), (b"QUJ=", 2), (b"QUB=", 2), (b"R0lGQR==", 5)):
+        if _dec_ex(lib, s, 4)[0::2] != (3, fb):
+            return False
+    return True
+
+
+def test_unmodified_variants_pass(tmp_path):
+    assert _variant_pins_pass(_bind_ex(_compile(tmp_path, "orig_ex", open(SRC).read())))
+
+
+@pytest.mark.parametrize("name", sorted(VARIANT_MUTANTS))
+def test_variant_mutant_is_caught(tmp_path, name):
+    old, new = VARIANT_MUTANTS[name]
+    lib = _bind_ex(_compile(tmp_path, name, mutate(open(SRC).read(), old, new, variants=True)))
+    assert not _variant_pins_pass(lib), f"planted mistake {name} survived the pins"
