@@ -47,6 +47,7 @@ typedef enum {
   B64_OK = 0,
   B64_ERR_INVALID_CHAR = 1,
   B64_ERR_BAD_LENGTH = 2,
+  B64_ERR_NONCANONICAL = 3, /* B64_FLAG_STRICT_TAIL: non-zero trailing bits */
   B64_ERR_ARG = -1,
   B64_ERR_CUDA = -2,
   B64_ERR_NOMEM = -3,
@@ -247,6 +248,40 @@ int b64_server_replay(b64_server *server, int64_t n, const double *t_arrival_us,
                       double *latency_us, int32_t *status);
 /* Stops the engine, waits for work in flight, frees everything. */
 void b64_server_destroy(b64_server *server);
+
+/* ---- variants (Section 2: base64url, omitted padding; Appendix A) ----
+ * Flags for the _ex calls (0 = the calls above):
+ *   B64_FLAG_URL          base64url alphabet: values 62 and 63 are '-' and '_'
+ *                         (then '+' and '/' are invalid characters).
+ *   B64_FLAG_NOPAD        encode writes no '=' (output b64_encoded_len_ex);
+ *                         decode also accepts a final group of 2 or 3
+ *                         characters (1 or 2 bytes); padded input is still
+ *                         accepted; a final group of 1 character is
+ *                         B64_ERR_BAD_LENGTH at m - 1.
+ *   B64_FLAG_STRICT_TAIL  decode applies Appendix A's check of the final
+ *                         group: the bits dropped by the last data character
+ *                         must be zero, else B64_ERR_NONCANONICAL with
+ *                         first_bad = that character (invalid characters and
+ *                         the length rule are reported first). Ignored by
+ *                         encode, whose output always has zero bits. */
+#define B64_FLAG_URL 1
+#define B64_FLAG_NOPAD 2
+#define B64_FLAG_STRICT_TAIL 4
+
+size_t b64_encoded_len_ex(size_t n, int flags);
+size_t b64_decoded_cap_ex(size_t m, int flags);
+size_t b64_encode_ex(const uint8_t *src, size_t n, char *dst, int flags, gb64_stream_t stream);
+int b64_decode_ex(const char *src, size_t m, uint8_t *dst, size_t *outlen, size_t *first_bad,
+                  int flags, gb64_stream_t stream);
+int b64_decode_async_ex(const char *src, size_t m, uint8_t *dst, b64_result *d_result, int flags,
+                        gb64_stream_t stream);
+int b64_batch_out_offsets_ex(int decode, const int64_t *in_off, int64_t nmsg, int64_t *out_off,
+                             int flags, gb64_stream_t stream);
+int b64_encode_batch_ex(const uint8_t *src, const int64_t *in_off, int64_t nmsg, char *dst,
+                        int64_t *out_off, int flags, gb64_stream_t stream);
+int b64_decode_batch_ex(const char *src, const int64_t *in_off, int64_t nmsg, uint8_t *dst,
+                        int64_t *out_off, int32_t *status, int64_t *first_bad, int64_t *outlen,
+                        int flags, gb64_stream_t stream);
 
 /* Human-readable name of a b64_status value (static string). */
 const char *b64_status_str(int status);

@@ -103,9 +103,15 @@ int read_and_clear_faults() {
   return (a | b) ? B64_ERR_TIMEOUT : B64_OK;
 }
 
+constexpr int kAllFlags = B64_FLAG_URL | B64_FLAG_NOPAD | B64_FLAG_STRICT_TAIL;
+
 // Shared by the synchronous and host-buffer decodes: checks and enqueues.
 int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, int flags = 0) {
+  if (flags & ~kAllFlags) {
+    set_error("unknown flag bits 0x%x", flags & ~kAllFlags);
+    return B64_ERR_ARG;
+  }
   if (!d_result) {
     set_error("d_result is null");
     return B64_ERR_ARG;
@@ -114,7 +120,7 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
     set_error("d_result must be 8-byte aligned");
     return B64_ERR_ARG;
   }
-  const size_t cap = b64_decoded_cap(m);
+  const size_t cap = (size_t)decoded_cap_flags(m, (uint32_t)flags);
   if (m > 0 && !src) {
     set_error("src is null");
     return B64_ERR_ARG;
@@ -130,7 +136,7 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
   cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(b64_result), stream);
   if (e != cudaSuccess) return cuda_status(e, "decode: clearing the result");
   e = launch_decode(reinterpret_cast<const uint8_t*>(src), m, decode_body_end(m), dst, d_result,
-                    stream, single_config(1, m));
+                    stream, single_config(1, m), (uint32_t)flags);
   if (e != cudaSuccess) return cuda_status(e, "decode: launch");
   return B64_OK;
 }
@@ -149,14 +155,26 @@ size_t b64_encoded_len(size_t n) {
 
 size_t b64_decoded_cap(size_t m) { return 3 * (m / 4); }
 
-size_t b64_encode(const uint8_t* src, size_t n, char* dst, gb64_stream_t stream) {
+size_t b64_encoded_len_ex(size_t n, int flags) {
+  const size_t groups = n / 3 + (n % 3 != 0);
+  if (groups > SIZE_MAX / 4) return SIZE_MAX;
+  return (size_t)encoded_len_flags(n, (uint32_t)flags);
+}
+
+size_t b64_decoded_cap_ex(size_t m, int flags) { return (size_t)decoded_cap_flags(m, (uint32_t)flags); }
+
+size_t b64_encode_ex(const uint8_t* src, size_t n, char* dst, int flags, gb64_stream_t stream) {
   clear_error();
+  if (flags & ~kAllFlags) {
+    set_error("unknown flag bits 0x%x", flags & ~kAllFlags);
+    return SIZE_MAX;
+  }
   if (n == 0) return 0;
   if (!src || !dst) {
     set_error("%s is null", src ? "dst" : "src");
     return SIZE_MAX;
   }
-  const size_t m = b64_encoded_len(n);
+  const size_t m = b64_encoded_len_ex(n, flags);
   if (m == SIZE_MAX) {
     set_error("input length %zu overflows the output length", n);
     return SIZE_MAX;
@@ -166,12 +184,23 @@ size_t b64_encode(const uint8_t* src, size_t n, char* dst, gb64_stream_t stream)
     return SIZE_MAX;
   }
   cudaError_t e = launch_encode(src, n, reinterpret_cast<uint8_t*>(dst),
-                                reinterpret_cast<cudaStream_t>(stream), single_config(0, n));
+                                reinterpret_cast<cudaStream_t>(stream), single_config(0, n),
+                                (uint32_t)flags);
   if (e != cudaSuccess) {
     cuda_status(e, "encode: launch");
     return SIZE_MAX;
   }
   return m;
+}
+
+size_t b64_encode(const uint8_t* src, size_t n, char* dst, gb64_stream_t stream) {
+  return b64_encode_ex(src, n, dst, 0, stream);
+}
+
+int b64_decode_async_ex(const char* src, size_t m, uint8_t* dst, b64_result* d_result, int flags,
+                        gb64_stream_t stream) {
+  clear_error();
+  return decode_enqueue(src, m, dst, d_result, reinterpret_cast<cudaStream_t>(stream), flags);
 }
 
 int b64_decode_async(const char* src, size_t m, uint8_t* dst, b64_result* d_result,
@@ -180,8 +209,8 @@ int b64_decode_async(const char* src, size_t m, uint8_t* dst, b64_result* d_resu
   return decode_enqueue(src, m, dst, d_result, reinterpret_cast<cudaStream_t>(stream));
 }
 
-int b64_decode(const char* src, size_t m, uint8_t* dst, size_t* outlen, size_t* first_bad,
-               gb64_stream_t stream) {
+int b64_decode_ex(const char* src, size_t m, uint8_t* dst, size_t* outlen, size_t* first_bad,
+                  int flags, gb64_stream_t stream) {
   clear_error();
   if (!outlen || !first_bad) {
     set_error("outlen and first_bad must not be null");
@@ -198,7 +227,7 @@ int b64_decode(const char* src, size_t m, uint8_t* dst, size_t* outlen, size_t* 
   DecodeScratch* sc = decode_scratch(di->device, &e);
   if (!sc) return cuda_status(e, "decode: result scratch");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int rc = decode_enqueue(src, m, dst, sc->dev, s);
+  int rc = decode_enqueue(src, m, dst, sc->dev, s, flags);
   if (rc != B64_OK) return rc;
   e = cudaMemcpyAsync(sc->host, sc->dev, sizeof(b64_result), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -209,11 +238,17 @@ int b64_decode(const char* src, size_t m, uint8_t* dst, size_t* outlen, size_t* 
   return sc->host->status;
 }
 
+int b64_decode(const char* src, size_t m, uint8_t* dst, size_t* outlen, size_t* first_bad,
+               gb64_stream_t stream) {
+  return b64_decode_ex(src, m, dst, outlen, first_bad, 0, stream);
+}
+
 const char* b64_status_str(int status) {
   switch (status) {
     case B64_OK: return "B64_OK";
     case B64_ERR_INVALID_CHAR: return "B64_ERR_INVALID_CHAR";
     case B64_ERR_BAD_LENGTH: return "B64_ERR_BAD_LENGTH";
+    case B64_ERR_NONCANONICAL: return "B64_ERR_NONCANONICAL";
     case B64_ERR_ARG: return "B64_ERR_ARG";
     case B64_ERR_CUDA: return "B64_ERR_CUDA";
     case B64_ERR_NOMEM: return "B64_ERR_NOMEM";

@@ -31,10 +31,11 @@ constexpr int64_t kScanPerBlock = (int64_t)kScanThreads * kScanItems;
 constexpr int64_t kNoBad = INT64_MAX;
 
 // ----------------------------------------------------------------- scan
-__device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, int64_t& outv,
-                                           int64_t& tiles) {
+__device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, uint32_t flags,
+                                           int64_t& outv, int64_t& tiles) {
   if (len < 0) len = 0;
-  outv = decode ? 3 * (len / 4) : 4 * ((len + 2) / 3);
+  outv = decode ? (int64_t)decoded_cap_flags((uint64_t)len, flags)
+                : (int64_t)encoded_len_flags((uint64_t)len, flags);
   tiles = (len + tile - 1) / tile;
 }
 
@@ -85,7 +86,7 @@ __device__ __forceinline__ void block_exclusive_scan2(int64_t& a, int64_t& b, in
 
 __global__ void __launch_bounds__(kScanThreads)
     k_scan_local(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
-                 int64_t* __restrict__ out_off, int64_t* __restrict__ tile_off,
+                 uint32_t flags, int64_t* __restrict__ out_off, int64_t* __restrict__ tile_off,
                  int64_t* __restrict__ part_out, int64_t* __restrict__ part_tiles) {
   const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
   int64_t vo[kScanItems], vt[kScanItems];
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kScanThreads)
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t j = base + i;
     vo[i] = vt[i] = 0;
-    if (j < nmsg) msg_values(decode, in_off[j + 1] - in_off[j], tile, vo[i], vt[i]);
+    if (j < nmsg) msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, vo[i], vt[i]);
     so += vo[i];
     st += vt[i];
   }
@@ -211,7 +212,7 @@ struct DescMsgs {
 // message's last tile also codes the partial group with its padding).
 template <int NT>
 __device__ __forceinline__ void encode_tile(const Msg& m, int64_t t0, int64_t tile,
-                                            const uint8_t* T) {
+                                            const uint8_t* T, uint32_t flags) {
   const uint32_t tid = threadIdx.x;
   const uint32_t len = (uint32_t)tmin<int64_t>(tile, m.len - t0);
   const uint8_t* sp = m.src + t0;
@@ -228,44 +229,8 @@ __device__ __forceinline__ void encode_tile(const Msg& m, int64_t t0, int64_t ti
     const uint8_t* p = sp + 12 * nu + 3 * tid;
     const uint32_t cnt = min(3u, rest - 3 * tid);
     const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
-    store4_any(dp + 16 * nu + 4 * tid, enc_tail_group(b0, b1, b2, cnt, T));
+    store_tail_group(dp + 16 * nu + 4 * tid, enc_tail_group(b0, b1, b2, cnt, T), cnt, flags);
   }
-}
-
-// Final characters of one message (same rules as the single-buffer decode).
-__device__ uint32_t batch_dec_final(const uint8_t* src, uint64_t m, uint64_t body_end,
-                                    uint8_t* dst, const uint8_t* D,
-                                    unsigned long long* first_bad) {
-  const uint32_t cnt = (uint32_t)(m - body_end);
-  const uint8_t* p = src + body_end;
-  if (cnt == 4 && m % 4 == 0) {
-    const uint32_t c[4] = {p[0], p[1], p[2], p[3]};
-    uint32_t npad = 0;
-    if (c[3] == kPadChar) npad = (c[2] == kPadChar) ? 2 : 1;
-    uint32_t v[4];
-    for (uint32_t k = 0; k < 4; ++k) {
-      const bool is_pad = k >= 4 - npad;
-      const uint32_t d = D[c[k]];
-      if (!is_pad && (d & kBadFlag)) {
-        atomicMin(first_bad, (unsigned long long)(body_end + k));
-        return 0;
-      }
-      v[k] = is_pad ? 0u : d;
-    }
-    const uint32_t val = (v[0] << 18) | (v[1] << 12) | (v[2] << 6) | v[3];
-    uint8_t* o = dst + body_end / 4 * 3;
-    o[0] = (uint8_t)(val >> 16);
-    if (npad < 2) o[1] = (uint8_t)(val >> 8);
-    if (npad < 1) o[2] = (uint8_t)val;
-    return 3 - npad;
-  }
-  for (uint32_t k = 0; k < cnt; ++k) {
-    if (D[p[k]] & kBadFlag) {
-      atomicMin(first_bad, (unsigned long long)(body_end + k));
-      break;
-    }
-  }
-  return 0;
 }
 
 // Decodes tile [t0, t0 + tile) of message m (Algorithm 2 per unit; the tile
@@ -274,7 +239,7 @@ __device__ uint32_t batch_dec_final(const uint8_t* src, uint64_t m, uint64_t bod
 template <int NT>
 __device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t tile,
                                             const uint8_t* D, unsigned long long* fb,
-                                            int64_t* outlen_j) {
+                                            int64_t* outlen_j, uint32_t flags) {
   const uint32_t tid = threadIdx.x;
   const uint64_t mlen = (uint64_t)m.len;
   const uint64_t body_end = decode_body_end(mlen);
@@ -312,16 +277,17 @@ __device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t t
     }
   }
   if (tid == NT - 1 && body_end >= t0 && body_end < t0 + len)
-    *outlen_j = batch_dec_final(m.src, mlen, body_end, m.out, D, fb);
+    *outlen_j = dec_final_group(m.src, mlen, body_end, m.out, D, fb, flags);
 }
 
 // Persistent tile walk: CTA b owns tiles [b*T/G, (b+1)*T/G) of the
 // T = tile_off[nmsg] tiles, in order.
 template <int NT, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_encode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile) {
+    k_batch_encode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
+                   uint32_t flags) {
   __shared__ uint8_t T[64];
-  init_tables(T, nullptr);
+  init_tables(T, nullptr, flags & kFlagUrl);
   const int64_t total = tile_off[nmsg];
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
   int64_t t = (int64_t)blockIdx.x * per;
@@ -332,16 +298,17 @@ __global__ void __launch_bounds__(NT)
   int64_t j = owner_of(tile_off, nmsg, t);
   for (; t < t_end; ++t) {
     while (__ldg(tile_off + j + 1) <= t) ++j;
-    encode_tile<NT>(ms.get(j), (t - __ldg(tile_off + j)) * tile, tile, T);
+    encode_tile<NT>(ms.get(j), (t - __ldg(tile_off + j)) * tile, tile, T, flags);
   }
 }
 
 template <int NT, class Msgs>
 __global__ void __launch_bounds__(NT)
     k_batch_decode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
-                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
+                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
+                   uint32_t flags) {
   __shared__ uint8_t D[256];
-  init_tables(nullptr, D);
+  init_tables(nullptr, D, flags & kFlagUrl);
   const int64_t total = tile_off[nmsg];
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
   int64_t t = (int64_t)blockIdx.x * per;
@@ -353,31 +320,25 @@ __global__ void __launch_bounds__(NT)
   for (; t < t_end; ++t) {
     while (__ldg(tile_off + j + 1) <= t) ++j;
     decode_tile<NT>(ms.get(j), (uint64_t)(t - __ldg(tile_off + j)) * tile, tile, D,
-                    reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j);
+                    reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j, flags);
   }
 }
 
-// Per-message status: first bad character wins, then the length rule.
+// Per-message status: first bad character wins, then the length rule, then
+// Appendix A's check (decoder of the final group returned a negative code).
 template <class Msgs>
 __global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restrict__ status,
                                       int64_t* __restrict__ first_bad,
-                                      int64_t* __restrict__ outlen) {
+                                      int64_t* __restrict__ outlen, uint32_t flags) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nmsg) return;
-  const int64_t m = max((long long)0, (long long)msgs.len(j));
-  const int64_t fb = first_bad[j];
-  if (fb != kNoBad) {
-    status[j] = B64_ERR_INVALID_CHAR;
-    outlen[j] = 0;
-  } else if (m % 4 != 0) {
-    status[j] = B64_ERR_BAD_LENGTH;
-    first_bad[j] = m - m % 4;
-    outlen[j] = 0;
-  } else {
-    status[j] = B64_OK;
-    first_bad[j] = m;
-    outlen[j] = (int64_t)(decode_body_end((uint64_t)m) / 4 * 3) + outlen[j];
-  }
+  const uint64_t m = (uint64_t)max((long long)0, (long long)msgs.len(j));
+  const uint64_t body_end = decode_body_end(m);
+  const int64_t final = (body_end < m) ? outlen[j] : 0;
+  const FinalStatus f = final_status(m, body_end, (unsigned long long)first_bad[j], final, flags);
+  status[j] = f.status;
+  first_bad[j] = f.first_bad;
+  outlen[j] = f.outlen;
 }
 
 // Initial per-message decode results for descriptor batches.
@@ -397,13 +358,15 @@ size_t batch_scratch_bytes(int64_t nmsg) {
 
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
                           int64_t* tile_off, int64_t tile, void* scratch_parts,
-                          int64_t* first_bad, int64_t* outlen, cudaStream_t stream) {
+                          int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
+                          uint32_t flags) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
   int64_t* part_out = static_cast<int64_t*>(scratch_parts);
   int64_t* part_tiles = part_out + std::max<int64_t>(nparts, 1);
   if (nparts > 0) {
-    k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, out_off,
-                                                                tile_off, part_out, part_tiles);
+    k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
+                                                                out_off, tile_off, part_out,
+                                                                part_tiles);
     k_scan_parts<<<1, kScanThreads, 0, stream>>>(part_out, part_tiles, nparts);
   }
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
@@ -416,39 +379,40 @@ namespace {
 template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                         int32_t* status, int64_t* first_bad, int64_t* outlen,
-                        const BatchConfig& cfg, const DeviceInfo* di, cudaStream_t stream) {
+                        const BatchConfig& cfg, const DeviceInfo* di, uint32_t flags,
+                        cudaStream_t stream) {
   const int grid = di->sm_count * cfg.blocks_per_sm;
   if (!decode) {
-    k_batch_encode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile);
+    k_batch_encode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile, flags);
     return cudaGetLastError();
   }
   k_batch_decode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile, first_bad,
-                                                    outlen);
+                                                    outlen, flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
   k_batch_decode_finish<Msgs><<<(unsigned)blocks, 256, 0, stream>>>(msgs, nmsg, status, first_bad,
-                                                                   outlen);
+                                                                   outlen, flags);
   return cudaGetLastError();
 }
 
 template <class Msgs>
 cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                             int32_t* status, int64_t* first_bad, int64_t* outlen,
-                            const BatchConfig& cfg, cudaStream_t stream) {
+                            const BatchConfig& cfg, uint32_t flags, cudaStream_t stream) {
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
     case 128:
       return launch_work<128>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              stream);
+                              flags, stream);
     case 512:
       return launch_work<512>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              stream);
+                              flags, stream);
     default:
       return launch_work<256>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              stream);
+                              flags, stream);
   }
 }
 }  // namespace
@@ -456,7 +420,7 @@ cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const in
 cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
                               const int64_t* tile_off, int32_t* status, int64_t* first_bad,
                               int64_t* outlen, const BatchConfig& cfg, bool init_results,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, uint32_t flags) {
   if (decode && init_results) {
     const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
     k_batch_decode_init<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, first_bad, outlen);
@@ -464,18 +428,18 @@ cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uin
     if (e != cudaSuccess) return e;
   }
   return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, tile_off, status, first_bad, outlen,
-                         cfg, stream);
+                         cfg, flags, stream);
 }
 
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
   cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, cfg.tile,
                                 a.parts, a.decode ? a.first_bad : nullptr,
-                                a.decode ? a.outlen : nullptr, a.stream);
+                                a.decode ? a.outlen : nullptr, a.stream, a.flags);
   if (e != cudaSuccess) return e;
   // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
   PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
   return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen, cfg,
-                         a.stream);
+                         a.flags, a.stream);
 }
 
 int batch_read_and_clear_fault(unsigned int* out) {

@@ -29,6 +29,7 @@ struct BatchArgs {
   int64_t* first_bad = nullptr;
   int64_t* outlen = nullptr;
   cudaStream_t stream = nullptr;
+  uint32_t flags = 0;  // variants of Section 2 / Appendix A (B64_FLAG_*)
 };
 
 // One message of a descriptor batch: its bytes anywhere in device memory and
@@ -46,7 +47,7 @@ struct MsgDesc {
 cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
                               const int64_t* tile_off, int32_t* status, int64_t* first_bad,
                               int64_t* outlen, const BatchConfig& cfg, bool init_results,
-                              cudaStream_t stream);
+                              cudaStream_t stream, uint32_t flags = 0);
 
 // Bytes of scratch a batch of nmsg messages needs (tile_off + scan parts).
 size_t batch_scratch_bytes(int64_t nmsg);
@@ -61,7 +62,7 @@ inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** tile_off,
 // are initialised when non-null.
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
                           int64_t* tile_off, int64_t tile, void* parts, int64_t* first_bad,
-                          int64_t* outlen, cudaStream_t stream);
+                          int64_t* outlen, cudaStream_t stream, uint32_t flags = 0);
 
 // Offsets + the persistent tile kernel (+ the decode finish kernel).
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);

@@ -39,6 +39,16 @@ int check_offsets_args(const int64_t* in_off, int64_t nmsg, const int64_t* out_o
   return B64_OK;
 }
 
+constexpr int kAllFlags = B64_FLAG_URL | B64_FLAG_NOPAD | B64_FLAG_STRICT_TAIL;
+
+int check_flags(int flags) {
+  if (flags & ~kAllFlags) {
+    set_error("unknown flag bits 0x%x", flags & ~kAllFlags);
+    return B64_ERR_ARG;
+  }
+  return B64_OK;
+}
+
 int run_batch(BatchArgs a) {
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(a.nmsg), a.stream);
@@ -59,10 +69,11 @@ using namespace gb64;
 
 extern "C" {
 
-int b64_batch_out_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
-                          gb64_stream_t stream) {
+int b64_batch_out_offsets_ex(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
+                             int flags, gb64_stream_t stream) {
   clear_error();
   int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc == B64_OK) rc = check_flags(flags);
   if (rc != B64_OK) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void* scratch = nullptr;
@@ -72,17 +83,23 @@ int b64_batch_out_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
   void* parts;
   batch_scratch_split(scratch, nmsg, &tile_off, &parts);
   e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, tile_off, 1 << 20, parts, nullptr,
-                    nullptr, s);
+                    nullptr, s, (uint32_t)flags);
   cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e == cudaSuccess) e = ef;
   if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets");
   return B64_OK;
 }
 
-int b64_encode_batch(const uint8_t* src, const int64_t* in_off, int64_t nmsg, char* dst,
-                     int64_t* out_off, gb64_stream_t stream) {
+int b64_batch_out_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
+                          gb64_stream_t stream) {
+  return b64_batch_out_offsets_ex(decode, in_off, nmsg, out_off, 0, stream);
+}
+
+int b64_encode_batch_ex(const uint8_t* src, const int64_t* in_off, int64_t nmsg, char* dst,
+                        int64_t* out_off, int flags, gb64_stream_t stream) {
   clear_error();
   int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc == B64_OK) rc = check_flags(flags);
   if (rc != B64_OK) return rc;
   if (nmsg > 0 && (!src || !dst)) {
     set_error("src and dst must not be null");
@@ -96,14 +113,21 @@ int b64_encode_batch(const uint8_t* src, const int64_t* in_off, int64_t nmsg, ch
   a.dst = reinterpret_cast<uint8_t*>(dst);
   a.out_off = out_off;
   a.stream = reinterpret_cast<cudaStream_t>(stream);
+  a.flags = (uint32_t)flags;
   return run_batch(a);
 }
 
-int b64_decode_batch(const char* src, const int64_t* in_off, int64_t nmsg, uint8_t* dst,
-                     int64_t* out_off, int32_t* status, int64_t* first_bad, int64_t* outlen,
-                     gb64_stream_t stream) {
+int b64_encode_batch(const uint8_t* src, const int64_t* in_off, int64_t nmsg, char* dst,
+                     int64_t* out_off, gb64_stream_t stream) {
+  return b64_encode_batch_ex(src, in_off, nmsg, dst, out_off, 0, stream);
+}
+
+int b64_decode_batch_ex(const char* src, const int64_t* in_off, int64_t nmsg, uint8_t* dst,
+                        int64_t* out_off, int32_t* status, int64_t* first_bad, int64_t* outlen,
+                        int flags, gb64_stream_t stream) {
   clear_error();
   int rc = check_offsets_args(in_off, nmsg, out_off);
+  if (rc == B64_OK) rc = check_flags(flags);
   if (rc != B64_OK) return rc;
   if (nmsg > 0 && (!src || !dst || !status || !first_bad || !outlen)) {
     set_error("src, dst, status, first_bad and outlen must not be null");
@@ -125,7 +149,15 @@ int b64_decode_batch(const char* src, const int64_t* in_off, int64_t nmsg, uint8
   a.first_bad = first_bad;
   a.outlen = outlen;
   a.stream = reinterpret_cast<cudaStream_t>(stream);
+  a.flags = (uint32_t)flags;
   return run_batch(a);
+}
+
+int b64_decode_batch(const char* src, const int64_t* in_off, int64_t nmsg, uint8_t* dst,
+                     int64_t* out_off, int32_t* status, int64_t* first_bad, int64_t* outlen,
+                     gb64_stream_t stream) {
+  return b64_decode_batch_ex(src, in_off, nmsg, dst, out_off, status, first_bad, outlen, 0,
+                             stream);
 }
 
 }  // extern "C"

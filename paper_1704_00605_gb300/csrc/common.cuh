@@ -16,6 +16,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/gb64.h"
+#include "rules.h"
+
 namespace gb64 {
 
 template <typename T>
@@ -30,19 +33,24 @@ __host__ __device__ __forceinline__ T tmax(T a, T b) {
 constexpr uint32_t kPadChar = 0x3D;  // '='
 constexpr uint32_t kBadFlag = 0x80;  // decode-table flag for bytes outside the alphabet
 
-// Table 3: 6-bit value -> ASCII code, by range.
-__host__ __device__ constexpr uint32_t alphabet_char(uint32_t v) {
-  return v < 26 ? v + 65 : v < 52 ? v + 71 : v < 62 ? v - 4 : v == 62 ? v - 19 : v - 16;
+// Table 3: 6-bit value -> ASCII code, by range; base64url (Section 2) maps
+// 62 and 63 to '-' and '_'.
+__host__ __device__ constexpr uint32_t alphabet_char(uint32_t v, bool url = false) {
+  return v < 26 ? v + 65
+       : v < 52 ? v + 71
+       : v < 62 ? v - 4
+       : v == 62 ? (url ? 0x2Du : v - 19)
+                 : (url ? 0x5Fu : v - 16);
 }
 
 // Fills the shared tables. enc: 64 bytes; dec: 256 bytes (either may be null).
-__device__ __forceinline__ void init_tables(uint8_t* enc, uint8_t* dec) {
+__device__ __forceinline__ void init_tables(uint8_t* enc, uint8_t* dec, bool url = false) {
   if (dec) {
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) dec[i] = (uint8_t)kBadFlag;
     __syncthreads();
   }
   for (uint32_t v = threadIdx.x; v < 64; v += blockDim.x) {
-    const uint32_t c = alphabet_char(v);
+    const uint32_t c = alphabet_char(v, url);
     if (enc) enc[v] = (uint8_t)c;
     if (dec) dec[c] = (uint8_t)v;
   }
@@ -332,6 +340,72 @@ __device__ __forceinline__ void store4_any(uint8_t* p, uint32_t w) {
     p[2] = (uint8_t)(w >> 16);
     p[3] = (uint8_t)(w >> 24);
   }
+}
+
+// Writes the final group's characters: 4 with padding, or cnt + 1 (2 or 3)
+// when padding is omitted (a full group, cnt = 3, always writes 4).
+__device__ __forceinline__ void store_tail_group(uint8_t* p, uint32_t w, uint32_t cnt,
+                                                 uint32_t flags) {
+  if (cnt == 3 || !(flags & kFlagNoPad)) {
+    store4_any(p, w);
+  } else {
+    for (uint32_t k = 0; k <= cnt; ++k) p[k] = (uint8_t)(w >> (8 * k));
+  }
+}
+
+// ------------------------------------------------------- final group
+// Final characters [body_end, m) of a message: a last quad that may end in
+// "=" or "==" (m % 4 == 0), or 1-3 characters of an incomplete group (an
+// unpadded final group under kFlagNoPad, else only validated). Lowers
+// *first_bad on an invalid character. Returns the bytes written (0..3), or
+// -(1 + k) when Appendix A's check (kFlagStrictTail) fails at character
+// body_end + k: with "==" (or 2 unpadded characters) the second character
+// must have (value * 16) mod 256 = 0, with "=" (or 3) the third must have
+// (value * 64) mod 256 = 0.
+static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t m, uint64_t body_end,
+                                            uint8_t* dst, const uint8_t* D,
+                                            unsigned long long* first_bad, uint32_t flags) {
+  const uint32_t cnt = (uint32_t)(m - body_end);
+  const uint8_t* p = src + body_end;
+  uint8_t* o = dst + body_end / 4 * 3;
+  const bool strict = (flags & kFlagStrictTail) != 0;
+  if (cnt == 4 && m % 4 == 0) {
+    const uint32_t c[4] = {p[0], p[1], p[2], p[3]};
+    uint32_t npad = 0;
+    if (c[3] == kPadChar) npad = (c[2] == kPadChar) ? 2 : 1;
+    uint32_t v[4];
+    for (uint32_t k = 0; k < 4; ++k) {
+      const bool is_pad = k >= 4 - npad;
+      const uint32_t d = D[c[k]];
+      if (!is_pad && (d & kBadFlag)) {
+        atomicMin(first_bad, (unsigned long long)(body_end + k));
+        return 0;
+      }
+      v[k] = is_pad ? 0u : d;
+    }
+    if (strict && npad == 2 && (v[1] & 15u)) return -2;
+    if (strict && npad == 1 && (v[2] & 3u)) return -3;
+    const uint32_t val = (v[0] << 18) | (v[1] << 12) | (v[2] << 6) | v[3];
+    o[0] = (uint8_t)(val >> 16);
+    if (npad < 2) o[1] = (uint8_t)(val >> 8);
+    if (npad < 1) o[2] = (uint8_t)val;
+    return 3 - (int)npad;
+  }
+  uint32_t v[3] = {0, 0, 0};
+  for (uint32_t k = 0; k < cnt; ++k) {
+    const uint32_t d = D[p[k]];
+    if (d & kBadFlag) {
+      atomicMin(first_bad, (unsigned long long)(body_end + k));
+      return 0;
+    }
+    if (k < 3) v[k] = d;
+  }
+  if (!(flags & kFlagNoPad) || cnt < 2) return 0;  // the length rule decides
+  if (strict && cnt == 2 && (v[1] & 15u)) return -2;
+  if (strict && cnt == 3 && (v[2] & 3u)) return -3;
+  o[0] = (uint8_t)((v[0] << 2) | (v[1] >> 4));
+  if (cnt == 3) o[1] = (uint8_t)(((v[1] & 15u) << 4) | (v[2] >> 2));
+  return (int)cnt - 1;
 }
 
 // ------------------------------------------------------ error reduction

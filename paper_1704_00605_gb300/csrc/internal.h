@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gb64.h"
+#include "rules.h"
 
 namespace gb64 {
 
@@ -43,22 +44,14 @@ size_t single_smem_bytes(int decode, const TileConfig& c);
 // Single-buffer encode of n >= 1 bytes; picks the TMA kernel when src and
 // dst are 16-byte aligned, else the generic one.
 cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStream_t stream,
-                          const TileConfig& cfg);
+                          const TileConfig& cfg, uint32_t flags = 0);
 
 // Single-buffer decode of m characters. Characters [0, body_end) must be
 // whole quads of the alphabet; [body_end, m) are the final characters
 // (padding rules). The caller has set *res to all-ones bytes on stream.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
-                          b64_result* res, cudaStream_t stream, const TileConfig& cfg);
-
-// Start of the final characters of a whole message of m characters.
-#ifdef __CUDACC__
-__host__ __device__
-#endif
-inline uint64_t decode_body_end(uint64_t m) {
-  if (m == 0) return 0;
-  return (m % 4 == 0) ? m - 4 : m - m % 4;
-}
+                          b64_result* res, cudaStream_t stream, const TileConfig& cfg,
+                          uint32_t flags = 0);
 
 // Reads and clears the fault words of every kernel file (current device).
 int read_and_clear_faults();

@@ -45,6 +45,7 @@ struct EncArgs {
   uint8_t* dst;
   uint32_t upt;
   uint32_t stages;
+  uint32_t flags;
 };
 
 struct DecArgs {
@@ -55,10 +56,13 @@ struct DecArgs {
   b64_result* res;
   uint32_t upt;
   uint32_t stages;
+  uint32_t flags;
 };
 
 // ------------------------------------------------------------- encode/TMA
-template <int NT>
+// FLAGS (kFlagUrl | kFlagNoPad) is a compile-time parameter: the default
+// instantiation (0) carries no variant code at all.
+template <int NT, uint32_t FLAGS>
 __global__ void __launch_bounds__(NT) k_encode_tma(EncArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t T[64];
@@ -73,7 +77,7 @@ __global__ void __launch_bounds__(NT) k_encode_tma(EncArgs a) {
     for (uint32_t s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  init_tables(T, nullptr);
+  init_tables(T, nullptr, (FLAGS & kFlagUrl) != 0);
 
   auto issue = [&](uint64_t t, uint32_t s) {
     const uint64_t off = t * tile_in;
@@ -119,7 +123,11 @@ __global__ void __launch_bounds__(NT) k_encode_tma(EncArgs a) {
         const uint8_t* p = a.src + off + done + 3 * g;
         const uint32_t cnt = min(3u, rest - 3 * g);
         const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
-        store4_any(out + 16 * (size_t)nu + 4 * g, enc_tail_group(b0, b1, b2, cnt, T));
+        if (FLAGS & kFlagNoPad)
+          store_tail_group(out + 16 * (size_t)nu + 4 * g, enc_tail_group(b0, b1, b2, cnt, T), cnt,
+                           kFlagNoPad);
+        else
+          store4_any(out + 16 * (size_t)nu + 4 * g, enc_tail_group(b0, b1, b2, cnt, T));
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -143,9 +151,9 @@ __global__ void __launch_bounds__(NT) k_encode_tma(EncArgs a) {
 // ---------------------------------------------------------- encode/generic
 template <int NT>
 __global__ void __launch_bounds__(NT) k_encode_any(const uint8_t* __restrict__ src, uint64_t n,
-                                                   uint8_t* __restrict__ dst) {
+                                                   uint8_t* __restrict__ dst, uint32_t flags) {
   __shared__ uint8_t T[64];
-  init_tables(T, nullptr);
+  init_tables(T, nullptr, flags & kFlagUrl);
   const uint64_t nunits = n / 12;
   const uint64_t stride = (uint64_t)gridDim.x * NT;
   for (uint64_t u = (uint64_t)blockIdx.x * NT + threadIdx.x; u < nunits; u += stride) {
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_encode_any(const uint8_t* __restrict__ s
       const uint8_t* p = src + done + 3 * g;
       const uint32_t cnt = min(3u, rest - 3 * g);
       const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
-      store4_any(dst + 16 * nunits + 4 * g, enc_tail_group(b0, b1, b2, cnt, T));
+      store_tail_group(dst + 16 * nunits + 4 * g, enc_tail_group(b0, b1, b2, cnt, T), cnt, flags);
     }
   }
 }
@@ -185,43 +193,6 @@ __device__ __forceinline__ unsigned long long dec_body_quad(const uint8_t* p, ui
   return ~0ull;
 }
 
-// Final characters [body_end, m) of a message: a last quad that may end in
-// "=" or "==" (m % 4 == 0), or 1-3 characters of an incomplete group. Lowers
-// *first_bad on an invalid character; returns the bytes written (0..3).
-__device__ uint32_t dec_final(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
-                              const uint8_t* D, unsigned long long* first_bad) {
-  const uint32_t cnt = (uint32_t)(m - body_end);
-  const uint8_t* p = src + body_end;
-  if (cnt == 4 && m % 4 == 0) {
-    uint32_t c[4] = {p[0], p[1], p[2], p[3]};
-    uint32_t npad = 0;
-    if (c[3] == kPadChar) npad = (c[2] == kPadChar) ? 2 : 1;
-    uint32_t v[4];
-    for (uint32_t k = 0; k < 4; ++k) {
-      const bool is_pad = k >= 4 - npad;
-      const uint32_t d = D[c[k]];
-      if (!is_pad && (d & kBadFlag)) {
-        atomicMin(first_bad, (unsigned long long)(body_end + k));
-        return 0;
-      }
-      v[k] = is_pad ? 0u : d;
-    }
-    const uint32_t val = (v[0] << 18) | (v[1] << 12) | (v[2] << 6) | v[3];
-    uint8_t* o = dst + body_end / 4 * 3;
-    o[0] = (uint8_t)(val >> 16);
-    if (npad < 2) o[1] = (uint8_t)(val >> 8);
-    if (npad < 1) o[2] = (uint8_t)val;
-    return 3 - npad;
-  }
-  for (uint32_t k = 0; k < cnt; ++k) {
-    if (D[p[k]] & kBadFlag) {
-      atomicMin(first_bad, (unsigned long long)(body_end + k));
-      break;
-    }
-  }
-  return 0;
-}
-
 // Runs in every CTA after its work: the last CTA to arrive computes the
 // status (first bad character wins, then the length rule).
 __device__ void dec_finish(const DecArgs& a, bool timed_out) {
@@ -241,18 +212,11 @@ __device__ void dec_finish(const DecArgs& a, bool timed_out) {
     r->first_bad = (int64_t)a.m;
     r->outlen = 0;
     r->status = B64_ERR_TIMEOUT;
-  } else if (fb != ~0ull) {
-    r->first_bad = (int64_t)fb;
-    r->outlen = 0;
-    r->status = B64_ERR_INVALID_CHAR;
-  } else if (a.m % 4 != 0) {
-    r->first_bad = (int64_t)(a.m - a.m % 4);
-    r->outlen = 0;
-    r->status = B64_ERR_BAD_LENGTH;
   } else {
-    r->first_bad = (int64_t)a.m;
-    r->outlen = (int64_t)(a.body_end / 4 * 3) + final_bytes;
-    r->status = B64_OK;
+    const FinalStatus f = final_status(a.m, a.body_end, fb, final_bytes, a.flags);
+    r->first_bad = f.first_bad;
+    r->outlen = f.outlen;
+    r->status = f.status;
   }
   __threadfence();
 }
@@ -276,7 +240,7 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a) {
     for (uint32_t s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  init_tables(nullptr, D);
+  init_tables(nullptr, D, a.flags & kFlagUrl);
 
   auto issue = [&](uint64_t t, uint32_t s) {
     const uint64_t off = t * tile_c;
@@ -342,8 +306,7 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a) {
     }
     // final characters of the message
     if (tid == NT - 1 && a.body_end >= off && a.body_end < off + len) {
-      const uint32_t nb = dec_final(a.src, a.m, a.body_end, a.dst, D, first_bad);
-      a.res->outlen = nb;
+      a.res->outlen = dec_final_group(a.src, a.m, a.body_end, a.dst, D, first_bad, a.flags);
     }
 
     fence_proxy_async_smem();
@@ -381,7 +344,7 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a) {
 template <int NT>
 __global__ void __launch_bounds__(NT) k_decode_any(DecArgs a) {
   __shared__ uint8_t D[256];
-  init_tables(nullptr, D);
+  init_tables(nullptr, D, a.flags & kFlagUrl);
   unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(&a.res->first_bad);
   const uint64_t nunits = a.body_end / 16;
   const uint64_t stride = (uint64_t)gridDim.x * NT;
@@ -403,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_decode_any(DecArgs a) {
       if (b != ~0ull) atomicMin(first_bad, b);
     }
     if (threadIdx.x == NT - 1 && a.body_end < a.m) {
-      a.res->outlen = dec_final(a.src, a.m, a.body_end, a.dst, D, first_bad);
+      a.res->outlen = dec_final_group(a.src, a.m, a.body_end, a.dst, D, first_bad, a.flags);
     }
   }
   dec_finish(a, false);
@@ -487,27 +450,32 @@ int resident_ctas(int fitting, const TileConfig& c) {
 
 template <int NT>
 cudaError_t launch_encode_nt(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStream_t stream,
-                             const TileConfig& cfg, const DeviceInfo* di) {
+                             const TileConfig& cfg, const DeviceInfo* di, uint32_t flags) {
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) &
                         15u) == 0;
   if (aligned) {
-    EncArgs a{src, n, dst, (uint32_t)cfg.upt, (uint32_t)cfg.stages};
+    EncArgs a{src, n, dst, (uint32_t)cfg.upt, (uint32_t)cfg.stages, flags};
     const uint64_t tile_in = (uint64_t)NT * cfg.upt * 12u;
     const size_t smem = (size_t)cfg.stages * tile_in;
+    const uint32_t f = flags & (kFlagUrl | kFlagNoPad);
+    auto kernel = f == 0                          ? k_encode_tma<NT, 0>
+                  : f == kFlagUrl                 ? k_encode_tma<NT, kFlagUrl>
+                  : f == kFlagNoPad               ? k_encode_tma<NT, kFlagNoPad>
+                                                  : k_encode_tma<NT, kFlagUrl | kFlagNoPad>;
     int bps = 0;
-    cudaError_t e = prepare(k_encode_tma<NT>, smem, NT, &bps);
+    cudaError_t e = prepare(kernel, smem, NT, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = (n + tile_in - 1) / tile_in;
     const int grid =
         (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * resident_ctas(bps, cfg));
-    k_encode_tma<NT><<<grid, NT, smem, stream>>>(a);
+    kernel<<<grid, NT, smem, stream>>>(a);
     return cudaGetLastError();
   }
   const uint64_t units = n / 12 + 1;
   const int grid =
       (int)std::max<uint64_t>(1, std::min<uint64_t>((units + NT - 1) / NT, (uint64_t)di->sm_count * 8));
-  k_encode_any<NT><<<grid, NT, 0, stream>>>(src, n, dst);
+  k_encode_any<NT><<<grid, NT, 0, stream>>>(src, n, dst, flags);
   return cudaGetLastError();
 }
 
@@ -543,25 +511,26 @@ cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileC
 }  // namespace
 
 cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStream_t stream,
-                          const TileConfig& cfg) {
+                          const TileConfig& cfg, uint32_t flags) {
   if (!valid_config(cfg)) return cudaErrorInvalidValue;
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
-    case 128: return launch_encode_nt<128>(src, n, dst, stream, cfg, di);
-    case 512: return launch_encode_nt<512>(src, n, dst, stream, cfg, di);
-    default: return launch_encode_nt<256>(src, n, dst, stream, cfg, di);
+    case 128: return launch_encode_nt<128>(src, n, dst, stream, cfg, di, flags);
+    case 512: return launch_encode_nt<512>(src, n, dst, stream, cfg, di, flags);
+    default: return launch_encode_nt<256>(src, n, dst, stream, cfg, di, flags);
   }
 }
 
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
-                          b64_result* res, cudaStream_t stream, const TileConfig& cfg) {
+                          b64_result* res, cudaStream_t stream, const TileConfig& cfg,
+                          uint32_t flags) {
   if (!valid_config(cfg)) return cudaErrorInvalidValue;
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
-  DecArgs a{src, m, body_end, dst, res, 0, 0};
+  DecArgs a{src, m, body_end, dst, res, 0, 0, flags};
   switch (cfg.threads) {
     case 128: return launch_decode_nt<128>(a, stream, cfg, di);
     case 512: return launch_decode_nt<512>(a, stream, cfg, di);

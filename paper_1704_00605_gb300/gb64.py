@@ -19,6 +19,10 @@ from . import build as _build
 B64_OK = 0
 B64_ERR_INVALID_CHAR = 1
 B64_ERR_BAD_LENGTH = 2
+B64_ERR_NONCANONICAL = 3
+B64_FLAG_URL = 1
+B64_FLAG_NOPAD = 2
+B64_FLAG_STRICT_TAIL = 4
 B64_ERR_ARG = -1
 B64_ERR_CUDA = -2
 B64_ERR_NOMEM = -3
@@ -119,6 +123,14 @@ def lib() -> ctypes.CDLL:
         "b64_server_replay": (i32, [vp, i64, vp, vp, vp, vp, vp, vp]),
         "b64_server_destroy": (None, [vp]),
         "b64_decode_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp]),
+        "b64_encoded_len_ex": (sz, [sz, i32]),
+        "b64_decoded_cap_ex": (sz, [sz, i32]),
+        "b64_encode_ex": (sz, [vp, sz, vp, i32, vp]),
+        "b64_decode_ex": (i32, [vp, sz, vp, psz, psz, i32, vp]),
+        "b64_decode_async_ex": (i32, [vp, sz, vp, vp, i32, vp]),
+        "b64_batch_out_offsets_ex": (i32, [i32, vp, i64, vp, i32, vp]),
+        "b64_encode_batch_ex": (i32, [vp, vp, i64, vp, vp, i32, vp]),
+        "b64_decode_batch_ex": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -488,3 +500,119 @@ class Server:
 
 def b64_server_create(**cfg) -> Server:
     return Server(**cfg)
+
+
+# ------------------------------------------------ variants (flags, _ex calls)
+def b64_encoded_len_ex(n: int, flags: int) -> int:
+    return int(lib().b64_encoded_len_ex(n, flags))
+
+
+def b64_decoded_cap_ex(m: int, flags: int) -> int:
+    return int(lib().b64_decoded_cap_ex(m, flags))
+
+
+def b64_encode_ex(src, flags: int, dst=None, stream=None):
+    torch = _torch()
+    _check_u8(src, "src")
+    n = src.numel()
+    m = b64_encoded_len_ex(n, flags)
+    if dst is None:
+        dst = torch.empty(max(m, 1), dtype=torch.uint8, device=src.device)
+    _check_u8(dst, "dst")
+    if dst.numel() < m:
+        raise ValueError("dst is too small")
+    with torch.cuda.device(src.device):
+        r = lib().b64_encode_ex(_ptr(src), n, _ptr(dst), flags, _stream(stream, src.device))
+    if r == SIZE_MAX:
+        raise Gb64Error(B64_ERR_ARG, b64_last_error())
+    return dst[:m]
+
+
+def b64_decode_ex(src, flags: int, dst=None, stream=None):
+    """Synchronous decode with flags. Returns ``(status, outlen, first_bad, dst)``."""
+    torch = _torch()
+    _check_u8(src, "src")
+    m = src.numel()
+    cap = b64_decoded_cap_ex(m, flags)
+    if dst is None:
+        dst = torch.empty(max(cap, 1), dtype=torch.uint8, device=src.device)
+    _check_u8(dst, "dst")
+    if dst.numel() < cap:
+        raise ValueError(f"dst holds {dst.numel()} bytes; decoding may write {cap}")
+    outlen = ctypes.c_size_t(0)
+    first_bad = ctypes.c_size_t(0)
+    with torch.cuda.device(src.device):
+        st = lib().b64_decode_ex(_ptr(src), m, _ptr(dst) if cap else 0, ctypes.byref(outlen),
+                                 ctypes.byref(first_bad), flags, _stream(stream, src.device))
+    if st < 0:
+        raise Gb64Error(st, b64_last_error())
+    return st, int(outlen.value), int(first_bad.value), dst
+
+
+def b64_decode_async_ex(src, dst, result, flags: int, stream=None):
+    torch = _torch()
+    _check_u8(src, "src")
+    m = src.numel()
+    with torch.cuda.device(src.device):
+        st = lib().b64_decode_async_ex(_ptr(src), m, _ptr(dst) if b64_decoded_cap_ex(m, flags) else 0,
+                                       result.data_ptr(), flags, _stream(stream, src.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+
+
+def b64_batch_out_offsets_ex(decode: bool, in_off, flags: int, out_off=None, stream=None):
+    torch = _torch()
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
+    with torch.cuda.device(in_off.device):
+        st = lib().b64_batch_out_offsets_ex(1 if decode else 0, in_off.data_ptr(), nmsg,
+                                            out_off.data_ptr(), flags, _stream(stream, in_off.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return out_off
+
+
+def b64_encode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, stream=None):
+    torch = _torch()
+    _check_u8(src, "src")
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
+    if dst is None:
+        b64_batch_out_offsets_ex(False, in_off, flags, out_off, stream)
+        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=src.device)
+    with torch.cuda.device(src.device):
+        src, dst = _nonempty(src), _nonempty(dst)
+        st = lib().b64_encode_batch_ex(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
+                                       out_off.data_ptr(), flags, _stream(stream, src.device))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return dst, out_off
+
+
+def b64_decode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, status=None,
+                        first_bad=None, outlen=None, stream=None):
+    torch = _torch()
+    _check_u8(src, "src")
+    _check_off(in_off, "in_off")
+    nmsg = in_off.numel() - 1
+    dev = src.device
+    if out_off is None:
+        out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=dev)
+    if dst is None:
+        b64_batch_out_offsets_ex(True, in_off, flags, out_off, stream)
+        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=dev)
+    status = torch.empty(max(nmsg, 1), dtype=torch.int32, device=dev) if status is None else status
+    first_bad = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if first_bad is None else first_bad
+    outlen = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if outlen is None else outlen
+    with torch.cuda.device(dev):
+        src, dst = _nonempty(src), _nonempty(dst)
+        st = lib().b64_decode_batch_ex(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
+                                       out_off.data_ptr(), status.data_ptr(), first_bad.data_ptr(),
+                                       outlen.data_ptr(), flags, _stream(stream, dev))
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
+    return dst, out_off, status[:nmsg], first_bad[:nmsg], outlen[:nmsg]
