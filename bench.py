@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=1200)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["large", "batched", "serve"], default="large")
+    p.add_argument("--config", choices=["large", "batched", "serve", "sweep"], default="large")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched and serving sub-measurements of the default line")
     p.add_argument("--no-e2e", action="store_true")
@@ -408,8 +408,8 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000):
     doff = torch.from_numpy(off).to(dev)
     eoff = g.b64_batch_out_offsets(False, doff)
     enc = torch.empty(int(eoff[-1].item()), dtype=torch.uint8, device=dev)
-    dec_off = torch.empty(nmsg + 1, dtype=torch.int64, device=dev)
-    dec = torch.empty(int(data.size) + 16, dtype=torch.uint8, device=dev)
+    dec_off = g.b64_batch_out_offsets(True, eoff)  # decode outputs sit at capacity offsets
+    dec = torch.empty(int(dec_off[-1].item()) + 16, dtype=torch.uint8, device=dev)
     st = torch.empty(nmsg, dtype=torch.int32, device=dev)
     fb = torch.empty(nmsg, dtype=torch.int64, device=dev)
     ol = torch.empty(nmsg, dtype=torch.int64, device=dev)
@@ -573,6 +573,87 @@ def serve_line(args, d: Dist):
     }
 
 
+# ------------------------------------------------------ length sweep
+SWEEP_LENGTHS = [16, 64, 256, 1 << 10, 4 << 10, 16 << 10, 64 << 10, 256 << 10, 1 << 20,
+                 4 << 20, 16 << 20, 64 << 20, 256 << 20, 1 << 30]
+
+
+def run_sweep(args, d: Dist):
+    """Fig. 10's experiment on the GPU: encode and decode time against the
+    input length (uniform random bytes). For every length: one single-buffer
+    call (CUDA-event time per call, averaged over back-to-back calls; small
+    calls are launch-bound), and a batch of messages of that length totalling
+    about 256 MiB through the batched calls (lengths <= 1 MiB)."""
+    import torch
+
+    import paper_1704_00605_gb300 as pkg
+    from paper_1704_00605_gb300 import workloads as W
+
+    torch.cuda.set_device(d.local_rank)
+    g = pkg.load()
+    dev = torch.device("cuda", d.local_rank)
+    stream = torch.cuda.current_stream(dev)
+    big = W.counter_bytes_torch(7, 0, GIB, device=dev)
+    enc = torch.empty(g.b64_encoded_len(GIB), dtype=torch.uint8, device=dev)
+    dec = torch.empty(GIB + 16, dtype=torch.uint8, device=dev)
+    res = torch.empty(3, dtype=torch.int64, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e3  # microseconds per call
+
+    rows = []
+    for L in SWEEP_LENGTHS:
+        reps = max(3, min(2000, (256 << 20) // L))
+        src = big[:L]
+        m = g.b64_encoded_len(L)
+        e_us = timed(lambda: g.b64_encode(src, enc), reps)
+        d_us = timed(lambda: g.b64_decode_async(enc[:m], dec, res), reps)
+        row = {"length": L, "encode_us": round(e_us, 3), "decode_us": round(d_us, 3),
+               "encode_gbs": round(L / e_us / 1e3, 2), "decode_gbs": round(m / d_us / 1e3, 2)}
+        if L <= (1 << 20):
+            nmsg = max(1, (256 << 20) // L)
+            off = torch.arange(nmsg + 1, dtype=torch.int64, device=dev) * L
+            bsrc = big[:nmsg * L]
+            eoff = g.b64_batch_out_offsets(False, off)
+            benc = torch.empty(int(eoff[-1].item()), dtype=torch.uint8, device=dev)
+            doff = g.b64_batch_out_offsets(True, eoff)  # decode outputs sit at capacity offsets
+            bdec = torch.empty(int(doff[-1].item()) + 16, dtype=torch.uint8, device=dev)
+            st = torch.empty(nmsg, dtype=torch.int32, device=dev)
+            fb = torch.empty(nmsg, dtype=torch.int64, device=dev)
+            ol = torch.empty(nmsg, dtype=torch.int64, device=dev)
+            be = timed(lambda: g.b64_encode_batch(bsrc, off, benc, eoff), 5)
+            bd = timed(lambda: g.b64_decode_batch(benc, eoff, bdec, doff, st, fb, ol), 5)
+            assert int((st != 0).sum()) == 0
+            row.update({"batch_msgs": nmsg,
+                        "batch_encode_gbs": round(nmsg * L / be / 1e3, 1),
+                        "batch_decode_gbs": round(benc.numel() / bd / 1e3, 1),
+                        "batch_encode_msgs_per_s": round(nmsg / be * 1e6, 1),
+                        "batch_decode_msgs_per_s": round(nmsg / bd * 1e6, 1)})
+        rows.append(row)
+    return rows
+
+
+def sweep_line(args, d: Dist):
+    rows = run_sweep(args, d)
+    top = rows[-1]
+    return {
+        "metric": "encode/decode input GB/s against input length (Fig. 10 sweep)",
+        "value": top["encode_gbs"], "unit": "GB/s", "n_gpus": d.world, "steps": 1, "warmup": 1,
+        "ms_per_step": top["encode_us"] / 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic: uniform random bytes",
+        "config": {"workload": "length sweep 16 B .. 1 GiB, single calls and 256 MiB batches"},
+        "sweep": rows,
+    }
+
+
 # ------------------------------------------------------ reference arm
 def run_reference(args, d: Dist):
     """The CPU oracle as it stands, on the host cores, on bounded samples of
@@ -622,6 +703,8 @@ def main(argv=None):
         line = batched_line(args, d)
     elif args.config == "serve":
         line = serve_line(args, d)
+    elif args.config == "sweep":
+        line = sweep_line(args, d)
     else:
         line = run_large(args, d)
         if not args.small and not args.no_extras:

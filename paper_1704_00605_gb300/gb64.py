@@ -325,7 +325,7 @@ def b64_batch_out_offsets(decode: bool, in_off, out_off=None, stream=None):
     return out_off
 
 
-def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None):
+def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None, check_dst=False):
     """Encode packed messages; returns ``(dst, out_off)``."""
     torch = _torch()
     _check_u8(src, "src")
@@ -333,9 +333,13 @@ def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None):
     nmsg = in_off.numel() - 1
     if out_off is None:
         out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
-    if dst is None:
+    if dst is None or check_dst:
         b64_batch_out_offsets(False, in_off, out_off, stream)
-        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=src.device)
+        need = int(out_off[-1].item())
+        if dst is None:
+            dst = torch.empty(max(need, 1), dtype=torch.uint8, device=src.device)
+        elif dst.numel() < need:
+            raise ValueError(f"dst holds {dst.numel()} bytes; the batch needs {need}")
     with torch.cuda.device(src.device):
         src, dst = _nonempty(src), _nonempty(dst)
         st = lib().b64_encode_batch(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
@@ -346,8 +350,11 @@ def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None):
 
 
 def b64_decode_batch(src, in_off, dst=None, out_off=None, status=None, first_bad=None,
-                     outlen=None, stream=None):
-    """Decode packed messages; returns ``(dst, out_off, status, first_bad, outlen)``."""
+                     outlen=None, stream=None, check_dst=False):
+    """Decode packed messages; returns ``(dst, out_off, status, first_bad, outlen)``.
+    A caller-provided ``dst`` must hold the sum of the decode capacities
+    (``out_off[-1]``); ``check_dst=True`` verifies that first (one scan and a
+    host read)."""
     torch = _torch()
     _check_u8(src, "src")
     _check_off(in_off, "in_off")
@@ -355,9 +362,13 @@ def b64_decode_batch(src, in_off, dst=None, out_off=None, status=None, first_bad
     dev = src.device
     if out_off is None:
         out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=dev)
-    if dst is None:
+    if dst is None or check_dst:
         b64_batch_out_offsets(True, in_off, out_off, stream)
-        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=dev)
+        need = int(out_off[-1].item())
+        if dst is None:
+            dst = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        elif dst.numel() < need:
+            raise ValueError(f"dst holds {dst.numel()} bytes; the batch needs {need}")
     if status is None:
         status = torch.empty(max(nmsg, 1), dtype=torch.int32, device=dev)
     if first_bad is None:
@@ -594,7 +605,7 @@ def b64_encode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, stream=
 
 
 def b64_decode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, status=None,
-                        first_bad=None, outlen=None, stream=None):
+                        first_bad=None, outlen=None, stream=None, check_dst=False):
     torch = _torch()
     _check_u8(src, "src")
     _check_off(in_off, "in_off")
@@ -602,9 +613,13 @@ def b64_decode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, status=
     dev = src.device
     if out_off is None:
         out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=dev)
-    if dst is None:
+    if dst is None or check_dst:
         b64_batch_out_offsets_ex(True, in_off, flags, out_off, stream)
-        dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=dev)
+        need = int(out_off[-1].item())
+        if dst is None:
+            dst = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        elif dst.numel() < need:
+            raise ValueError(f"dst holds {dst.numel()} bytes; the batch needs {need}")
     status = torch.empty(max(nmsg, 1), dtype=torch.int32, device=dev) if status is None else status
     first_bad = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if first_bad is None else first_bad
     outlen = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if outlen is None else outlen
