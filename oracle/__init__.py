@@ -30,6 +30,7 @@ NONCANONICAL = 3
 FLAG_URL = 1
 FLAG_NOPAD = 2
 FLAG_STRICT_TAIL = 4
+FLAG_SKIP_WS = 8
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +81,9 @@ def _load():
         lib.oracle_decode_ex.argtypes = [vp, c_size, vp, ctypes.POINTER(c_size),
                                          ctypes.POINTER(c_size), ctypes.c_int]
         lib.oracle_decode_ex.restype = ctypes.c_int
+        lib.oracle_decode_ws.argtypes = [vp, c_size, vp, ctypes.POINTER(c_size),
+                                         ctypes.POINTER(c_size), ctypes.c_int]
+        lib.oracle_decode_ws.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -187,6 +191,7 @@ def decode_ex(chars, flags: int):
     out = np.empty(max(int(_load().oracle_decoded_cap_ex(src.size, flags)), 1), dtype=np.uint8)
     outlen = ctypes.c_size_t(0)
     first_bad = ctypes.c_size_t(0)
-    st = _load().oracle_decode_ex(_ptr(src), src.size, out.ctypes.data, ctypes.byref(outlen),
-                                  ctypes.byref(first_bad), flags)
+    fn = _load().oracle_decode_ws if flags & FLAG_SKIP_WS else _load().oracle_decode_ex
+    st = fn(_ptr(src), src.size, out.ctypes.data, ctypes.byref(outlen), ctypes.byref(first_bad),
+            flags)
     return int(st), out[: outlen.value].copy(), int(first_bad.value)

@@ -39,6 +39,7 @@
  */
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 /* Status codes of the decoder (same numbering as the C ABI, written out
  * separately here so that the oracle depends on nothing of the product). */
@@ -322,4 +323,39 @@ int oracle_decode_ex(const char *c, size_t m, uint8_t *p, size_t *outlen, size_t
   *outlen = k;
   *first_bad = m;
   return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Whitespace (Appendix B): with ORACLE_FLAG_SKIP_WS the decoder first
+ * removes the space, line-feed and carriage-return characters, the way
+ * Fig. 11 does (copy every byte, advance the write position only for bytes
+ * that are kept), remembering where each kept byte came from; it decodes
+ * the remaining characters with the other flags and reports first_bad as
+ * an index into the original input (m, the original length, on success).
+ * ---------------------------------------------------------------------- */
+#define ORACLE_FLAG_SKIP_WS 8
+
+static int is_space(unsigned char x) { return x == ' ' || x == '\n' || x == '\r'; }
+
+int oracle_decode_ws(const char *c, size_t m, uint8_t *p, size_t *outlen, size_t *first_bad,
+                     int flags) {
+  char *kept = (char *)malloc(m ? m : 1);
+  size_t *from = (size_t *)malloc((m ? m : 1) * sizeof(size_t));
+  if (!kept || !from) {
+    free(kept);
+    free(from);
+    return -3;
+  }
+  size_t q = 0;
+  for (size_t i = 0; i < m; i++) {
+    kept[q] = c[i];
+    from[q] = i;
+    q += !is_space((unsigned char)c[i]);
+  }
+  size_t fb = 0;
+  int st = oracle_decode_ex(kept, q, p, outlen, &fb, flags & ~ORACLE_FLAG_SKIP_WS);
+  *first_bad = (st == ORACLE_OK) ? m : from[fb];
+  free(kept);
+  free(from);
+  return st;
 }

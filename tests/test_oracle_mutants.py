@@ -140,6 +140,9 @@ VARIANT_MUTANTS = {
     "nopad_keeps_padding": ("      if (pad) p[k++] = PAD;\n    } else if", "      p[k++] = PAD;\n    } else if"),
     "nopad_tail_shift": ("      p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 4));\n    }\n  }",
                          "      p[k++] = (uint8_t)(((b * 16) % 256) + (cc / 8));\n    }\n  }"),
+    "ws_misses_cr": ("return x == ' ' || x == '\\n' || x == '\\r';", "return x == ' ' || x == '\\n';"),
+    "ws_first_bad_not_mapped": ("*first_bad = (st == ORACLE_OK) ? m : from[fb];",
+                                "*first_bad = (st == ORACLE_OK) ? m : fb;"),
 }
 
 
@@ -150,6 +153,8 @@ def _bind_ex(lib):
                                      ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.c_int]
     lib.oracle_decode_ex.restype = ctypes.c_int
+    lib.oracle_decode_ws.argtypes = lib.oracle_decode_ex.argtypes
+    lib.oracle_decode_ws.restype = ctypes.c_int
     return lib
 
 
@@ -162,7 +167,8 @@ def _enc_ex(lib, raw: bytes, flags: int) -> bytes:
 def _dec_ex(lib, s: bytes, flags: int):
     out = ctypes.create_string_buffer(3 * (len(s) // 4) + 8)
     ol, fb = ctypes.c_size_t(), ctypes.c_size_t()
-    st = lib.oracle_decode_ex(s, len(s), out, ctypes.byref(ol), ctypes.byref(fb), flags)
+    fn = lib.oracle_decode_ws if flags & 8 else lib.oracle_decode_ex
+    st = fn(s, len(s), out, ctypes.byref(ol), ctypes.byref(fb), flags)
     return st, out.raw[:ol.value], fb.value
 
 
@@ -192,6 +198,12 @@ def _variant_pins_pass(lib) -> bool:
     for s, fb in ((b"QR==", 1), (b"QI==", 1), (b"QUJ=", 2), (b"QUB=", 2), (b"R0lGQR==", 5)):
         if _dec_ex(lib, s, 4)[0::2] != (3, fb):
             return False
+    # whitespace removal (Appendix B): space, LF and CR anywhere; first_bad in
+    # original offsets
+    if _dec_ex(lib, b"QU\r\nJD R E\nVG\r\n", 8)[:2] != (0, b"ABCDEF"):
+        return False
+    if _dec_ex(lib, b"QU\r\nJD R!\nVG", 8)[0::2] != (1, 8):
+        return False
     return True
 
 

@@ -148,3 +148,72 @@ def test_strict_tail_precedence(oracle):
     assert oracle.decode_ex(b"YWJ", STRICT)[0::2] == (2, 0)
     assert oracle.decode_ex(b"YWJ", STRICT | NOPAD)[0::2] == (3, 2)
     assert oracle.decode_ex(b"YWI", STRICT | NOPAD)[0] == 0
+
+
+# ------------------------------------------------------- whitespace (App. B)
+SKIP_WS = 8
+WS = b" \n\r"
+
+
+def _sprinkle(rng, s: bytes, rate=0.03):
+    """Insert space/LF/CR before characters with probability `rate`
+    (Appendix B's test input has about 3 % whitespace); returns the string
+    and, for every character of s, its index in the result."""
+    out, where = bytearray(), []
+    for ch in s:
+        while rng.random() < rate:
+            out.append(WS[int(rng.integers(0, 3))])
+        where.append(len(out))
+        out.append(ch)
+    if rng.random() < 0.5:
+        out.extend(b"\r\n")
+    return bytes(out), where
+
+
+def test_skip_ws_matches_python_nonstrict(oracle):
+    rng = np.random.default_rng(21)
+    for n in list(range(0, 120)) + [999, 4096]:
+        raw = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        s, _ = _sprinkle(rng, base64.b64encode(raw))
+        st, out, fb = oracle.decode_ex(s, SKIP_WS)
+        assert (st, fb) == (0, len(s)) and out.tobytes() == raw
+        assert binascii.a2b_base64(s) == raw  # Python drops the whitespace too
+        assert _py_strict(bytes(c for c in s if c not in WS), False) == raw
+
+
+def test_skip_ws_first_bad_in_original_offsets(oracle):
+    from paper_1704_00605_gb300.workloads import NON_ALPHABET_NON_PAD
+
+    bad_set = [b for b in NON_ALPHABET_NON_PAD.tolist() if b not in WS]
+    rng = np.random.default_rng(22)
+    for trial in range(400):
+        raw = rng.integers(0, 256, int(rng.integers(1, 300)), dtype=np.uint8).tobytes()
+        enc = bytearray(base64.b64encode(raw))
+        q = int(rng.integers(0, len(enc) - 2))  # not the padding positions
+        enc[q] = bad_set[int(rng.integers(0, len(bad_set)))]
+        s, where = _sprinkle(rng, bytes(enc))
+        st, out, fb = oracle.decode_ex(s, SKIP_WS)
+        assert (st, fb) == (1, where[q]), (s, fb, where[q])
+
+
+def test_skip_ws_length_rule_and_equivalence(oracle):
+    rng = np.random.default_rng(23)
+    s, where = _sprinkle(rng, b"QUJDREVGQ", rate=0.3)
+    st, out, fb = oracle.decode_ex(s, SKIP_WS)
+    assert (st, fb) == (2, where[8])  # start of the incomplete group, original index
+    assert oracle.decode_ex(b" \n\r", SKIP_WS)[0::2] == (0, 3)  # nothing left: empty input
+    for base in (b"R0lGQUI=", b"R0lGQQ==", b"QUJDREVG"):
+        for q in range(len(base)):
+            for x in range(256):
+                t = bytearray(base)
+                t[q] = x
+                t = bytes(t)
+                if x in WS:
+                    continue
+                a, b = oracle.decode_ex(t, SKIP_WS), oracle.decode_ex(t, 0)
+                assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1])
+    # combined with the other flags: url alphabet, no padding, strict tail
+    raw = bytes(range(200))
+    s, _ = _sprinkle(rng, base64.urlsafe_b64encode(raw).rstrip(b"="))
+    st, out, fb = oracle.decode_ex(s, SKIP_WS | URL | NOPAD | STRICT)
+    assert st == 0 and out.tobytes() == raw
