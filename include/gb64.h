@@ -267,6 +267,13 @@ void b64_server_destroy(b64_server *server);
 #define B64_FLAG_URL 1
 #define B64_FLAG_NOPAD 2
 #define B64_FLAG_STRICT_TAIL 4
+/*   B64_FLAG_SKIP_WS      decode only, single buffer: space, line feed and
+ *                         carriage return are removed before decoding
+ *                         (Appendix B); first_bad is an index into the
+ *                         original input, outlen counts decoded bytes. Takes
+ *                         scratch of about m bytes from the stream-ordered
+ *                         allocator. Not accepted by encode or batches. */
+#define B64_FLAG_SKIP_WS 8
 
 size_t b64_encoded_len_ex(size_t n, int flags);
 size_t b64_decoded_cap_ex(size_t m, int flags);

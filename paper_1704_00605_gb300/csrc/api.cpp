@@ -104,12 +104,13 @@ int read_and_clear_faults() {
 }
 
 constexpr int kAllFlags = B64_FLAG_URL | B64_FLAG_NOPAD | B64_FLAG_STRICT_TAIL;
+constexpr int kDecodeFlags = kAllFlags | B64_FLAG_SKIP_WS;
 
 // Shared by the synchronous and host-buffer decodes: checks and enqueues.
 int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result,
                    cudaStream_t stream, int flags = 0) {
-  if (flags & ~kAllFlags) {
-    set_error("unknown flag bits 0x%x", flags & ~kAllFlags);
+  if (flags & ~kDecodeFlags) {
+    set_error("unknown flag bits 0x%x", flags & ~kDecodeFlags);
     return B64_ERR_ARG;
   }
   if (!d_result) {
@@ -135,6 +136,18 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
   }
   cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(b64_result), stream);
   if (e != cudaSuccess) return cuda_status(e, "decode: clearing the result");
+  if (flags & B64_FLAG_SKIP_WS) {
+    if (m == 0) return decode_enqueue(src, m, dst, d_result, stream, flags & ~B64_FLAG_SKIP_WS);
+    void* scratch = nullptr;
+    e = cudaMallocAsync(&scratch, ws_scratch_bytes(m), stream);
+    if (e != cudaSuccess) return cuda_status(e, "decode: whitespace scratch");
+    e = decode_ws_launch(reinterpret_cast<const uint8_t*>(src), m, dst, d_result, scratch,
+                         (uint32_t)flags, stream);
+    const cudaError_t ef = cudaFreeAsync(scratch, stream);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return cuda_status(e, "decode: whitespace launch");
+    return B64_OK;
+  }
   e = launch_decode(reinterpret_cast<const uint8_t*>(src), m, decode_body_end(m), dst, d_result,
                     stream, single_config(1, m), (uint32_t)flags);
   if (e != cudaSuccess) return cuda_status(e, "decode: launch");

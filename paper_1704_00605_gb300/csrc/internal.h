@@ -53,6 +53,12 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uin
                           b64_result* res, cudaStream_t stream, const TileConfig& cfg,
                           uint32_t flags = 0);
 
+// Whitespace-removing decode (ws.cu): scratch bytes for m characters, and
+// the launch (counts, scan, compaction, decode, mapping of first_bad).
+size_t ws_scratch_bytes(uint64_t m);
+cudaError_t decode_ws_launch(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
+                             void* scratch, uint32_t flags, cudaStream_t stream);
+
 // Reads and clears the fault words of every kernel file (current device).
 int read_and_clear_faults();
 int batch_read_and_clear_fault(unsigned int* out);
