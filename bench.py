@@ -618,6 +618,23 @@ def run_sweep(args, d: Dist):
         d_us = timed(lambda: g.b64_decode_async(enc[:m], dec, res), reps)
         row = {"length": L, "encode_us": round(e_us, 3), "decode_us": round(d_us, 3),
                "encode_gbs": round(L / e_us / 1e3, 2), "decode_gbs": round(m / d_us / 1e3, 2)}
+        if L <= (16 << 20):
+            # the same calls replayed from a CUDA graph: device time per call
+            # without the host-side cost of issuing it
+            k = 64
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            ge, gd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(ge, stream=side):
+                    for _ in range(k):
+                        g.b64_encode(src, enc)
+                with torch.cuda.graph(gd, stream=side):
+                    for _ in range(k):
+                        g.b64_decode_async(enc[:m], dec, res)
+            stream.wait_stream(side)
+            row["encode_us_graph"] = round(timed(ge.replay, 10) / k, 3)
+            row["decode_us_graph"] = round(timed(gd.replay, 10) / k, 3)
         if L <= (1 << 20):
             nmsg = max(1, (256 << 20) // L)
             off = torch.arange(nmsg + 1, dtype=torch.int64, device=dev) * L

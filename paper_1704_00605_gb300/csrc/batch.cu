@@ -247,12 +247,19 @@ __device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t t
   const uint32_t body = body_end > t0 ? (uint32_t)tmin<uint64_t>(len, body_end - t0) : 0u;
   const uint32_t nu = body / 16;
   unsigned long long bad = ~0ull;
-#pragma unroll 2
-  for (uint32_t u = tid; u < nu; u += NT) {
-    const uint4 w = load16_any(m.src + t0 + 16 * u, m.lo, m.hi);
-    uint32_t err = 0;
-    store12_any(m.out + t0 / 4 * 3 + 12 * u, dec_unit(w, D, err));
-    if ((err & kBadFlag) && bad == ~0ull) bad = t0 + 16 * u + dec_unit_first_bad(w, D);
+  const uint32_t lane = tid & 31u;
+  for (uint32_t base = 0; base < nu; base += NT) {
+    // the lanes of a warp own consecutive units, so they store together
+    const uint32_t u = base + tid;
+    uint3 o = make_uint3(0, 0, 0);
+    if (u < nu) {
+      const uint4 w = load16_any(m.src + t0 + 16 * u, m.lo, m.hi);
+      uint32_t err = 0;
+      o = dec_unit(w, D, err);
+      if ((err & kBadFlag) && bad == ~0ull) bad = t0 + 16 * u + dec_unit_first_bad(w, D);
+    }
+    const uint32_t u0 = base + (tid & ~31u);
+    if (u0 < nu) store12_warp(m.out + t0 / 4 * 3 + 12 * u0, o, lane, min(32u, nu - u0));
   }
   warp_min_to(fb, bad);
   const uint32_t nq = (body - 16 * nu) / 4;

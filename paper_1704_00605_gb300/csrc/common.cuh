@@ -353,6 +353,36 @@ __device__ __forceinline__ void store_tail_group(uint8_t* p, uint32_t w, uint32_
   }
 }
 
+// Warp-cooperative store: lane l writes its 12 bytes v at p + 12 * l, for
+// lanes l < nv (all 32 lanes must call it). At any alignment of p the lanes
+// write whole aligned 32-bit words, each built with a funnel shift from the
+// lane's own words and the previous lane's last word (shuffled up); only
+// the first and last few bytes of the warp's span use byte stores.
+__device__ __forceinline__ void store12_warp(uint8_t* p, uint3 v, uint32_t lane, uint32_t nv) {
+  const uint32_t r = reinterpret_cast<uintptr_t>(p) & 3u;
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, v.z, 1);
+  if (lane >= nv) return;
+  uint8_t* q = p + 12 * lane;
+  if (r == 0) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(q);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    return;
+  }
+  const uint32_t sh = 8 * (4 - r);
+  uint32_t* w = reinterpret_cast<uint32_t*>(q - r);  // aligned word holding q[0]
+  if (lane == 0) {
+    for (uint32_t k = 0; k < 4 - r; ++k) q[k] = (uint8_t)(v.x >> (8 * k));
+  } else {
+    w[0] = __funnelshift_r(prev, v.x, sh);
+  }
+  w[1] = __funnelshift_r(v.x, v.y, sh);
+  w[2] = __funnelshift_r(v.y, v.z, sh);
+  if (lane == nv - 1)
+    for (uint32_t k = 0; k < r; ++k) q[12 - r + k] = (uint8_t)(v.z >> (sh + 8 * k));
+}
+
 // ------------------------------------------------------- final group
 // Final characters [body_end, m) of a message: a last quad that may end in
 // "=" or "==" (m % 4 == 0), or 1-3 characters of an incomplete group (an

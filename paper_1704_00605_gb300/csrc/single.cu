@@ -361,13 +361,21 @@ __global__ void __launch_bounds__(NT) k_decode_any(DecArgs a0) {
   unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(&a.res->first_bad);
   const uint64_t nunits = a.body_end / 16;
   const uint64_t stride = (uint64_t)gridDim.x * NT;
+  const uint32_t lane = threadIdx.x & 31u;
   unsigned long long bad = ~0ull;
-  for (uint64_t u = (uint64_t)blockIdx.x * NT + threadIdx.x; u < nunits; u += stride) {
-    const uint4 w = load16_any(a.src + 16 * u, a.src, a.src + a.m);
-    uint32_t err = 0;
-    const uint3 o = dec_unit(w, D, err);
-    store12_any(a.dst + 12 * u, o);
-    if ((err & kBadFlag) && bad == ~0ull) bad = 16 * u + dec_unit_first_bad(w, D);
+  for (uint64_t base = (uint64_t)blockIdx.x * NT; base < nunits; base += stride) {
+    // consecutive lanes own consecutive units and store them together
+    const uint64_t u = base + threadIdx.x;
+    uint3 o = make_uint3(0, 0, 0);
+    if (u < nunits) {
+      const uint4 w = load16_any(a.src + 16 * u, a.src, a.src + a.m);
+      uint32_t err = 0;
+      o = dec_unit(w, D, err);
+      if ((err & kBadFlag) && bad == ~0ull) bad = 16 * u + dec_unit_first_bad(w, D);
+    }
+    const uint64_t u0 = base + (threadIdx.x & ~31u);
+    if (u0 < nunits)
+      store12_warp(a.dst + 12 * u0, o, lane, (uint32_t)tmin<uint64_t>(32, nunits - u0));
   }
   warp_min_to(first_bad, bad);
   if (blockIdx.x == 0) {

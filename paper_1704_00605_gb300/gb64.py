@@ -174,6 +174,27 @@ def _torch():
     return torch
 
 
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+_NULL = _Null()
+
+
+def _on(device):
+    """Device guard that costs nothing when ``device`` is already current."""
+    torch = _torch()
+    if isinstance(device, int):
+        idx = device
+    else:
+        idx = device.index if device.index is not None else torch.cuda.current_device()
+    return _NULL if idx == torch.cuda.current_device() else torch.cuda.device(idx)
+
+
 def _ptr(t) -> int:
     return t.data_ptr() if t is not None and t.numel() else 0
 
@@ -182,7 +203,7 @@ def _stream(stream, device):
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream(device)
-    return ctypes.c_void_p(stream.cuda_stream)
+    return stream.cuda_stream
 
 
 def _check_u8(t, name):
@@ -202,7 +223,7 @@ def b64_encode(src, dst=None, stream=None):
     _check_u8(dst, "dst")
     if dst.numel() < m:
         raise ValueError("dst is too small")
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         r = lib().b64_encode(_ptr(src), n, _ptr(dst), _stream(stream, src.device))
     if r == SIZE_MAX:
         raise Gb64Error(B64_ERR_ARG, b64_last_error())
@@ -222,7 +243,7 @@ def b64_decode(src, dst=None, stream=None):
         raise ValueError(f"dst holds {dst.numel()} bytes; decoding may write {cap}")
     outlen = ctypes.c_size_t(0)
     first_bad = ctypes.c_size_t(0)
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         st = lib().b64_decode(_ptr(src), m, _ptr(dst) if cap else 0, ctypes.byref(outlen),
                               ctypes.byref(first_bad), _stream(stream, src.device))
     if st < 0:
@@ -238,7 +259,7 @@ def b64_decode_async(src, dst, result, stream=None):
     if result.dtype != torch.int64 or result.numel() < 3 or not result.is_cuda:
         raise ValueError("result must be an int64 CUDA tensor with 3 entries")
     m = src.numel()
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         st = lib().b64_decode_async(_ptr(src), m, _ptr(dst) if b64_decoded_cap(m) else 0,
                                     result.data_ptr(), _stream(stream, src.device))
     if st != B64_OK:
@@ -317,7 +338,7 @@ def b64_batch_out_offsets(decode: bool, in_off, out_off=None, stream=None):
     nmsg = in_off.numel() - 1
     if out_off is None:
         out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
-    with torch.cuda.device(in_off.device):
+    with _on(in_off.device):
         st = lib().b64_batch_out_offsets(1 if decode else 0, in_off.data_ptr(), nmsg,
                                          out_off.data_ptr(), _stream(stream, in_off.device))
     if st != B64_OK:
@@ -340,7 +361,7 @@ def b64_encode_batch(src, in_off, dst=None, out_off=None, stream=None, check_dst
             dst = torch.empty(max(need, 1), dtype=torch.uint8, device=src.device)
         elif dst.numel() < need:
             raise ValueError(f"dst holds {dst.numel()} bytes; the batch needs {need}")
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         src, dst = _nonempty(src), _nonempty(dst)
         st = lib().b64_encode_batch(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
                                     out_off.data_ptr(), _stream(stream, src.device))
@@ -375,7 +396,7 @@ def b64_decode_batch(src, in_off, dst=None, out_off=None, status=None, first_bad
         first_bad = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev)
     if outlen is None:
         outlen = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev)
-    with torch.cuda.device(dev):
+    with _on(dev):
         src, dst = _nonempty(src), _nonempty(dst)
         st = lib().b64_decode_batch(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
                                     out_off.data_ptr(), status.data_ptr(), first_bad.data_ptr(),
@@ -532,7 +553,7 @@ def b64_encode_ex(src, flags: int, dst=None, stream=None):
     _check_u8(dst, "dst")
     if dst.numel() < m:
         raise ValueError("dst is too small")
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         r = lib().b64_encode_ex(_ptr(src), n, _ptr(dst), flags, _stream(stream, src.device))
     if r == SIZE_MAX:
         raise Gb64Error(B64_ERR_ARG, b64_last_error())
@@ -552,7 +573,7 @@ def b64_decode_ex(src, flags: int, dst=None, stream=None):
         raise ValueError(f"dst holds {dst.numel()} bytes; decoding may write {cap}")
     outlen = ctypes.c_size_t(0)
     first_bad = ctypes.c_size_t(0)
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         st = lib().b64_decode_ex(_ptr(src), m, _ptr(dst) if cap else 0, ctypes.byref(outlen),
                                  ctypes.byref(first_bad), flags, _stream(stream, src.device))
     if st < 0:
@@ -564,7 +585,7 @@ def b64_decode_async_ex(src, dst, result, flags: int, stream=None):
     torch = _torch()
     _check_u8(src, "src")
     m = src.numel()
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         st = lib().b64_decode_async_ex(_ptr(src), m, _ptr(dst) if b64_decoded_cap_ex(m, flags) else 0,
                                        result.data_ptr(), flags, _stream(stream, src.device))
     if st != B64_OK:
@@ -577,7 +598,7 @@ def b64_batch_out_offsets_ex(decode: bool, in_off, flags: int, out_off=None, str
     nmsg = in_off.numel() - 1
     if out_off is None:
         out_off = torch.empty(nmsg + 1, dtype=torch.int64, device=in_off.device)
-    with torch.cuda.device(in_off.device):
+    with _on(in_off.device):
         st = lib().b64_batch_out_offsets_ex(1 if decode else 0, in_off.data_ptr(), nmsg,
                                             out_off.data_ptr(), flags, _stream(stream, in_off.device))
     if st != B64_OK:
@@ -595,7 +616,7 @@ def b64_encode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, stream=
     if dst is None:
         b64_batch_out_offsets_ex(False, in_off, flags, out_off, stream)
         dst = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=src.device)
-    with torch.cuda.device(src.device):
+    with _on(src.device):
         src, dst = _nonempty(src), _nonempty(dst)
         st = lib().b64_encode_batch_ex(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
                                        out_off.data_ptr(), flags, _stream(stream, src.device))
@@ -623,7 +644,7 @@ def b64_decode_batch_ex(src, in_off, flags: int, dst=None, out_off=None, status=
     status = torch.empty(max(nmsg, 1), dtype=torch.int32, device=dev) if status is None else status
     first_bad = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if first_bad is None else first_bad
     outlen = torch.empty(max(nmsg, 1), dtype=torch.int64, device=dev) if outlen is None else outlen
-    with torch.cuda.device(dev):
+    with _on(dev):
         src, dst = _nonempty(src), _nonempty(dst)
         st = lib().b64_decode_batch_ex(_ptr(src), in_off.data_ptr(), nmsg, _ptr(dst),
                                        out_off.data_ptr(), status.data_ptr(), first_bad.data_ptr(),
