@@ -54,13 +54,16 @@ cudaError_t ensure_buffers(Pipe& p, size_t in_bytes, size_t out_bytes) {
   cudaError_t e = cudaStreamSynchronize(p.st[0]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p.st[1]);
   if (e != cudaSuccess) return e;
+  // grow to the larger of the old and new needs, so that alternating
+  // encode (48 MiB in, 64 MiB out) and decode (64 MiB in, 48 MiB out) calls
+  // stop reallocating after the first of each
+  const size_t ic = std::max(in_bytes, p.in_cap), oc = std::max(out_bytes, p.out_cap);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p.in[i]);
     cudaFree(p.out[i]);
     p.in[i] = p.out[i] = nullptr;
   }
   p.in_cap = p.out_cap = 0;
-  const size_t ic = std::max(in_bytes, p.in_cap), oc = std::max(out_bytes, p.out_cap);
   for (int i = 0; i < 2; ++i) {
     e = cudaMalloc(&p.in[i], ic);
     if (e == cudaSuccess) e = cudaMalloc(&p.out[i], oc);
