@@ -369,13 +369,34 @@ def run_e2e(g, data, d: Dist):
 
     step(0)
     assert np.array_equal(dec_np[:GIB], data[:GIB])
+    # the host link's own rate right now (pinned torch copies of 1 GiB)
+    dbuf = torch.empty(GIB, dtype=torch.uint8, device="cuda")
+    link = {}
+    for name, fn in (("h2d", lambda: dbuf.copy_(h_src[:GIB], non_blocking=True)),
+                     ("d2h", lambda: h_dec[:GIB].copy_(dbuf, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        link[name] = round(3 * GIB / (time.perf_counter() - t) / 1e9, 1)
+    del dbuf
     k = 3
     d.barrier()
     t0 = time.perf_counter()
     moved = 0
     hb = 0
+    t_enc = t_dec = 0.0
     for i in range(k):
-        n, m = step(i)
+        n = lengths[i % 3]
+        ta = time.perf_counter()
+        m = len(g.b64_encode_host(src_np[:n], enc_np))
+        tb = time.perf_counter()
+        st, outlen, fb, _ = g.b64_decode_host(enc_np[:m], dec_np)
+        t_enc += tb - ta
+        t_dec += time.perf_counter() - tb
+        assert st == 0 and outlen == n
         moved += n + m
         hb += n + m
     dt = time.perf_counter() - t0
@@ -383,7 +404,9 @@ def run_e2e(g, data, d: Dist):
     moved = d.reduce(float(moved), "sum")
     return {"value": round(moved / dt / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": int(hb // k), "d2h_bytes_per_step": int(hb // k),
-            "steps": k, "api": "b64_encode_host + b64_decode_host (pinned host buffers)"}
+            "steps": k, "api": "b64_encode_host + b64_decode_host (pinned host buffers)",
+            "encode_host_ms": round(t_enc / k * 1e3, 2), "decode_host_ms": round(t_dec / k * 1e3, 2),
+            "link_copy_gbs": link}
 
 
 # ------------------------------------------------------ batched workload

@@ -1,7 +1,8 @@
 // Host-buffer forms of encode and decode: the input is moved to the device
-// in chunks and the output moved back, with chunk i+1's host-to-device copy
-// overlapping chunk i's kernel and device-to-host copy (two internal streams
-// in ping-pong, both ordered after the caller's stream). Chunks are cut at
+// in chunks and the output moved back, with the host-to-device copy of one
+// chunk overlapping the kernel and device-to-host copy of the previous ones
+// (kStreams internal streams in rotation, all ordered after the caller's
+// stream). The link, not the kernels, bounds these calls. Chunks are cut at
 // multiples of 48 input bytes (encode) or 64 characters (decode) so every
 // chunk's device buffers stay 16-byte aligned and take the TMA kernels.
 #include <algorithm>
@@ -17,15 +18,16 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
 
 namespace {
 
-constexpr size_t kEncChunk = (size_t)48 << 20;  // input bytes per chunk (multiple of 48)
-constexpr size_t kDecChunk = (size_t)64 << 20;  // characters per chunk (multiple of 64)
+constexpr int kStreams = 3;
+constexpr size_t kEncChunk = (size_t)24 << 20;  // input bytes per chunk (multiple of 48)
+constexpr size_t kDecChunk = (size_t)32 << 20;  // characters per chunk (multiple of 64)
 
 struct Pipe {
   bool ready = false;
-  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaStream_t st[kStreams] = {};
   cudaEvent_t start = nullptr;
-  uint8_t* in[2] = {nullptr, nullptr};
-  uint8_t* out[2] = {nullptr, nullptr};
+  uint8_t* in[kStreams] = {};
+  uint8_t* out[kStreams] = {};
   size_t in_cap = 0, out_cap = 0;
   b64_result* res = nullptr;  // per-chunk decode results (device)
   b64_result* res_host = nullptr;
@@ -37,8 +39,9 @@ Pipe* pipe_for_device(int device, cudaError_t* err) {
   if ((int)pipes.size() <= device) pipes.resize(device + 1);
   Pipe& p = pipes[device];
   if (!p.ready) {
-    cudaError_t e = cudaStreamCreateWithFlags(&p.st[0], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.st[1], cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kStreams && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithFlags(&p.st[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       *err = e;
@@ -49,22 +52,30 @@ Pipe* pipe_for_device(int device, cudaError_t* err) {
   return &p;
 }
 
+cudaError_t sync_all(Pipe& p) {
+  cudaError_t first = cudaSuccess;
+  for (int i = 0; i < kStreams; ++i) {
+    const cudaError_t e = cudaStreamSynchronize(p.st[i]);
+    if (first == cudaSuccess) first = e;
+  }
+  return first;
+}
+
 cudaError_t ensure_buffers(Pipe& p, size_t in_bytes, size_t out_bytes) {
   if (p.in_cap >= in_bytes && p.out_cap >= out_bytes) return cudaSuccess;
-  cudaError_t e = cudaStreamSynchronize(p.st[0]);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p.st[1]);
+  cudaError_t e = sync_all(p);
   if (e != cudaSuccess) return e;
   // grow to the larger of the old and new needs, so that alternating
   // encode (48 MiB in, 64 MiB out) and decode (64 MiB in, 48 MiB out) calls
   // stop reallocating after the first of each
   const size_t ic = std::max(in_bytes, p.in_cap), oc = std::max(out_bytes, p.out_cap);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kStreams; ++i) {
     cudaFree(p.in[i]);
     cudaFree(p.out[i]);
     p.in[i] = p.out[i] = nullptr;
   }
   p.in_cap = p.out_cap = 0;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kStreams; ++i) {
     e = cudaMalloc(&p.in[i], ic);
     if (e == cudaSuccess) e = cudaMalloc(&p.out[i], oc);
     if (e != cudaSuccess) return e;
@@ -76,8 +87,7 @@ cudaError_t ensure_buffers(Pipe& p, size_t in_bytes, size_t out_bytes) {
 
 cudaError_t ensure_results(Pipe& p, size_t n) {
   if (p.res_cap >= n) return cudaSuccess;
-  cudaError_t e = cudaStreamSynchronize(p.st[0]);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p.st[1]);
+  cudaError_t e = sync_all(p);
   if (e != cudaSuccess) return e;
   cudaFree(p.res);
   cudaFreeHost(p.res_host);
@@ -95,8 +105,7 @@ cudaError_t ensure_results(Pipe& p, size_t n) {
 // Orders both pipe streams after the caller's stream.
 cudaError_t join_caller(Pipe& p, cudaStream_t caller) {
   cudaError_t e = cudaEventRecord(p.start, caller);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.st[0], p.start, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.st[1], p.start, 0);
+  for (int i = 0; i < kStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p.st[i], p.start, 0);
   return e;
 }
 
@@ -130,7 +139,7 @@ size_t b64_encode_host(const uint8_t* h_src, size_t n, char* h_dst, gb64_stream_
   e = ensure_buffers(*p, chunk, chunk / 3 * 4);
   if (e == cudaSuccess) e = join_caller(*p, reinterpret_cast<cudaStream_t>(stream));
   for (size_t off = 0, i = 0; e == cudaSuccess && off < n; off += chunk, ++i) {
-    const int b = (int)(i & 1);
+    const int b = (int)(i % kStreams);
     const size_t len = std::min(chunk, n - off);
     e = cudaMemcpyAsync(p->in[b], h_src + off, len, cudaMemcpyHostToDevice, p->st[b]);
     if (e == cudaSuccess) e = launch_encode(p->in[b], len, p->out[b], p->st[b], single_config(0, len));
@@ -138,9 +147,8 @@ size_t b64_encode_host(const uint8_t* h_src, size_t n, char* h_dst, gb64_stream_
       e = cudaMemcpyAsync(h_dst + off / 3 * 4, p->out[b], b64_encoded_len(len),
                           cudaMemcpyDeviceToHost, p->st[b]);
   }
-  cudaError_t e0 = cudaStreamSynchronize(p->st[0]);
-  cudaError_t e1 = cudaStreamSynchronize(p->st[1]);
-  if (e == cudaSuccess) e = e0 != cudaSuccess ? e0 : e1;
+  const cudaError_t es = sync_all(*p);
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) {
     cuda_status(e, "encode_host");
     return SIZE_MAX;
@@ -176,7 +184,7 @@ int b64_decode_host(const char* h_src, size_t m, uint8_t* h_dst, size_t* outlen,
   if (e != cudaSuccess) return cuda_status(e, "decode_host: buffers");
   const uint64_t body_end = decode_body_end(m);
   for (size_t i = 0; i < nchunks; ++i) {
-    const int b = (int)(i & 1);
+    const int b = (int)(i % kStreams);
     const size_t off = i * chunk;
     const size_t len = std::min(chunk, m - off);
     const bool last = (i + 1 == nchunks);
@@ -190,9 +198,8 @@ int b64_decode_host(const char* h_src, size_t m, uint8_t* h_dst, size_t* outlen,
                           cudaMemcpyDeviceToHost, p->st[b]);
     if (e != cudaSuccess) break;
   }
-  cudaError_t e0 = cudaStreamSynchronize(p->st[0]);
-  cudaError_t e1 = cudaStreamSynchronize(p->st[1]);
-  if (e == cudaSuccess) e = e0 != cudaSuccess ? e0 : e1;
+  const cudaError_t es = sync_all(*p);
+  if (e == cudaSuccess) e = es;
   if (e == cudaSuccess)
     e = cudaMemcpy(p->res_host, p->res, nchunks * sizeof(b64_result), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e, "decode_host");
