@@ -162,3 +162,45 @@ def test_batch_deterministic_and_stream_ordered(gb64, oracle):
         b, bo = gb64.b64_encode_batch(dev(data), dev(off), stream=s)
     s.synchronize()
     assert torch.equal(a, b) and torch.equal(ao, bo)
+
+
+def test_batch_calls_capture_into_a_cuda_graph(gb64, oracle):
+    """The batched calls enqueue only stream-ordered work (kernels, the
+    stream-ordered allocator), so they can be captured once and replayed:
+    a replay after new data was written into the same buffers codes it."""
+    import torch
+
+    data, off = W.batched(nmsg=3000, seed=71, median=600.0)
+    src, doff = dev(data), dev(off)
+    eoff = gb64.b64_batch_out_offsets(False, doff)
+    enc = torch.empty(int(eoff[-1].item()), dtype=torch.uint8, device="cuda")
+    dec_off = gb64.b64_batch_out_offsets(True, eoff)
+    dec = torch.empty(int(dec_off[-1].item()) + 16, dtype=torch.uint8, device="cuda")
+    n = off.size - 1
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    fb = torch.empty(n, dtype=torch.int64, device="cuda")
+    ol = torch.empty(n, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gb64.b64_encode_batch(src, doff, enc, eoff, stream=s)  # warm-up outside capture
+        gb64.b64_decode_batch(enc, eoff, dec, dec_off, st, fb, ol, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            gb64.b64_encode_batch(src, doff, enc, eoff, stream=s)
+            gb64.b64_decode_batch(enc, eoff, dec, dec_off, st, fb, ol, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for seed in (72, 73):
+        new = W.uniform_bytes(data.size, seed)
+        src.copy_(torch.from_numpy(new))
+        enc.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        exp, exp_off = oracle.encode_batch(new, off)
+        assert np.array_equal(enc.cpu().numpy(), exp)
+        assert int((st != 0).sum()) == 0
+        do = dec_off.cpu().numpy()
+        h = dec.cpu().numpy()
+        for j in range(0, n, 97):
+            assert np.array_equal(h[do[j]:do[j] + off[j + 1] - off[j]], new[off[j]:off[j + 1]])
