@@ -148,8 +148,12 @@ enum {
 /* A launch shape. Single kinds use threads, units_per_thread (12 input
  * bytes or 16 characters each; tile = threads * units_per_thread * unit),
  * stages (TMA stages in shared memory) and blocks_per_sm (0 = as many as
- * fit). Batch kinds use threads, tile (input bytes, multiple of 48, or
- * characters, multiple of 64) and blocks_per_sm. ms is a measured time. */
+ * fit). Batch kinds use threads, tile (input bytes per warp tile, a
+ * multiple of 384 up to 6144, or characters, a multiple of 512 up to
+ * 8192), stages (input stages per warp, 2..6; 0 = 4) and blocks_per_sm
+ * (0 = as many as fit); the shape's shared memory, threads / 32 * (stages *
+ * (tile + 32) + (decode only) 2 * (3 * tile / 4 + 32)) bytes, must stay
+ * within 219 KiB. ms is a measured time. */
 typedef struct {
   int32_t threads;
   int32_t units_per_thread;

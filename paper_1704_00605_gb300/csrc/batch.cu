@@ -6,13 +6,14 @@
 //      4 * ceil(n / 3) (encode) or 3 * floor(m / 4) (decode capacity); the
 //      tile count is ceil(length / tile). The exclusive sums become out_off
 //      (returned to the caller) and tile_off (scratch).
-//   2. k_batch_encode / k_batch_decode: a persistent grid; CTA b owns the
-//      contiguous tile range [b*T/G, (b+1)*T/G) of the T tiles, finds the
-//      owning message of its first tile by binary search in tile_off and
-//      advances through the following messages by a forward scan. Every tile
-//      is coded with the unit codecs of common.cuh; per-message padding
-//      (encode) and final quad, error index and length rule (decode) are
-//      handled in the tile that holds the message end.
+//   2. k_batch_code (encode or decode): a persistent grid in which every
+//      warp owns a contiguous range of the T tiles, finds the owning message
+//      of its first tile by binary search in tile_off and advances through
+//      the following messages by a forward scan. Tiles reach shared memory
+//      by bulk copies (TMA) several tiles ahead and are coded with the unit
+//      codecs of common.cuh; outputs leave by bulk stores. Per-message
+//      padding (encode) and final quad, error index and length rule
+//      (decode) are handled in the tile that holds the message end.
 //   3. k_batch_decode_finish: per-message status, first_bad and outlen.
 // All launches have fixed shapes, so a call can be captured in a CUDA graph.
 #include <algorithm>
@@ -24,6 +25,8 @@
 namespace gb64 {
 
 static __device__ unsigned int g_batch_fault;
+
+constexpr int kMaxBatchStages = 6;
 
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
@@ -208,68 +211,268 @@ struct DescMsgs {
   __device__ __forceinline__ void prepare(int64_t) {}
 };
 
-// Encodes tile [t0, t0 + tile) of message m (Algorithm 1 per unit; the
-// message's last tile also codes the partial group with its padding).
-template <int NT>
-__device__ __forceinline__ void encode_tile(const Msg& m, int64_t t0, int64_t tile,
-                                            const uint8_t* T, uint32_t flags) {
-  const uint32_t tid = threadIdx.x;
-  const uint32_t len = (uint32_t)tmin<int64_t>(tile, m.len - t0);
-  const uint8_t* sp = m.src + t0;
-  uint8_t* dp = m.out + t0 / 3 * 4;
-  const uint32_t nu = len / 12;
-#pragma unroll 2
-  for (uint32_t u = tid; u < nu; u += NT) {
-    const uint3 w = load12_any(sp + 12 * u, m.lo, m.hi);
-    store16_any(dp + 16 * u, enc_unit(w.x, w.y, w.z, T));
-  }
-  const uint32_t rest = len - 12 * nu;
-  const uint32_t ng = (rest + 2) / 3;
-  if (tid < ng) {
-    const uint8_t* p = sp + 12 * nu + 3 * tid;
-    const uint32_t cnt = min(3u, rest - 3 * tid);
-    const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
-    store_tail_group(dp + 16 * nu + 4 * tid, enc_tail_group(b0, b1, b2, cnt, T), cnt, flags);
+// ------------------------------------------------------ warp pipeline
+// Every warp walks its own contiguous range of tiles. Tile t of message j
+// holds input bytes [t0, t0 + len) of j (len <= tile). The tile's
+// 16-byte-aligned interior is copied into the warp's input stage by one bulk
+// copy, issued `stages` tiles ahead; stage position o + i holds input byte
+// t0 + i, o being the tile start's address mod 16, so positions [ia, ib)
+// are the copied ones. Units whose bytes reach outside [ia, ib) read global
+// memory instead. Every unit's output goes to the warp's output stage at
+// position o2 + i for output byte i (o2 = the output start's address mod
+// 16); the aligned interior of the tile's output leaves by one bulk store,
+// its two ragged ends (at most 15 bytes each) by byte stores.
+struct TileView {
+  const uint8_t* msrc;  // the message's input and output
+  uint8_t* mout;
+  const uint8_t* lo;    // bounds of aligned-word reads near the message ends
+  const uint8_t* hi;
+  uint8_t* dst;         // output of the tile's first unit
+  int64_t t0;           // offset of the tile in its message
+  int64_t mlen;
+  int64_t j;            // message index
+  uint32_t len;         // input bytes of the tile
+  uint32_t o;           // stage position of input byte t0
+  uint32_t ia, ib;
+};
+
+// The view of tile t, advancing the message cursor j (tile_off is
+// non-decreasing and t < tile_off[nmsg]).
+template <class Msgs>
+__device__ __forceinline__ TileView tile_view(const Msgs& ms, const int64_t* tile_off, int64_t t,
+                                              int64_t& j, int64_t tile, int64_t out_tile) {
+  while (__ldg(tile_off + j + 1) <= t) ++j;
+  const Msg m = ms.get(j);
+  const int64_t k = t - __ldg(tile_off + j);
+  TileView v;
+  v.msrc = m.src;
+  v.mout = m.out;
+  v.lo = m.lo;
+  v.hi = m.hi;
+  v.dst = m.out + k * out_tile;
+  v.t0 = k * tile;
+  v.mlen = m.len;
+  v.j = j;
+  v.len = (uint32_t)tmin<int64_t>(tile, m.len - v.t0);
+  const uintptr_t s = reinterpret_cast<uintptr_t>(m.src + v.t0);
+  const uintptr_t a = (s + 15u) & ~(uintptr_t)15u, b = (s + v.len) & ~(uintptr_t)15u;
+  v.o = (uint32_t)(s & 15u);
+  v.ia = v.o ? 16u : 0u;
+  v.ib = b > a ? v.ia + (uint32_t)(b - a) : v.ia;
+  return v;
+}
+
+// Issues the bulk copy of a tile's interior into its input stage (one lane;
+// the arrive publishes the view written before it).
+__device__ __forceinline__ void issue_tile(const TileView& v, uint8_t* in, uint64_t* bar) {
+  fence_proxy_async_smem();  // earlier generic reads of this stage come first
+  if (v.ib > v.ia) {
+    mbar_arrive_expect_tx(bar, v.ib - v.ia);
+    tma_load_1d(in + v.ia, v.msrc + v.t0 + (v.ia - v.o), v.ib - v.ia, bar);
+  } else {
+    mbar_arrive(bar);
   }
 }
 
-// Decodes tile [t0, t0 + tile) of message m (Algorithm 2 per unit; the tile
-// holding the message end also checks the final characters). Every thread
-// of the CTA must call it (warp-wide error reduction).
-template <int NT>
-__device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t tile,
-                                            const uint8_t* D, unsigned long long* fb,
-                                            int64_t* outlen_j, uint32_t flags) {
-  const uint32_t tid = threadIdx.x;
-  const uint64_t mlen = (uint64_t)m.len;
-  const uint64_t body_end = decode_body_end(mlen);
-  const uint32_t len = (uint32_t)tmin<uint64_t>(tile, mlen - t0);
-  const uint32_t body = body_end > t0 ? (uint32_t)tmin<uint64_t>(len, body_end - t0) : 0u;
-  const uint32_t nu = body / 16;
-  unsigned long long bad = ~0ull;
-  const uint32_t lane = tid & 31u;
-  for (uint32_t base = 0; base < nu; base += NT) {
-    // the lanes of a warp own consecutive units, so they store together
-    const uint32_t u = base + tid;
-    uint3 o = make_uint3(0, 0, 0);
-    if (u < nu) {
-      const uint4 w = load16_any(m.src + t0 + 16 * u, m.lo, m.hi);
-      uint32_t err = 0;
-      o = dec_unit(w, D, err);
-      if ((err & kBadFlag) && bad == ~0ull) bad = t0 + 16 * u + dec_unit_first_bad(w, D);
+// Writes output bytes [0, olen) of a tile, staged at out + (d mod 16), to d:
+// the aligned interior by one bulk store (always one commit group per
+// tile), the ends by lanes 0-14 and 16-30. The warp has fenced and synced.
+__device__ __forceinline__ void copy_out(uint8_t* d, uint32_t olen, const uint8_t* out,
+                                         uint32_t lane) {
+  const uintptr_t da = reinterpret_cast<uintptr_t>(d);
+  const uint32_t o2 = (uint32_t)(da & 15u);
+  const uintptr_t a = (da + 15u) & ~(uintptr_t)15u, b = (da + olen) & ~(uintptr_t)15u;
+  if (lane == 0) {
+    if (b > a) tma_store_1d(reinterpret_cast<void*>(a), out + (o2 ? 16u : 0u), (uint32_t)(b - a));
+    bulk_commit();
+  }
+  const uint32_t head = (uint32_t)(tmin<uintptr_t>(a, da + olen) - da);
+  const uint32_t ie = b > a ? (uint32_t)(b - da) : head;  // end of the interior
+  if (lane < head) {
+    d[lane] = out[o2 + lane];
+  } else if (lane >= 16u && lane - 16u < olen - ie) {
+    d[ie + lane - 16u] = out[o2 + ie + lane - 16u];
+  }
+}
+
+// Input words of the 12 tile bytes at off: from the stage when they were
+// all copied there, else from global memory (off + 12 <= the tile's length).
+__device__ __forceinline__ uint3 enc_load(const TileView& v, const uint8_t* in, const uint8_t* sp,
+                                          uint32_t off) {
+  const uint32_t p = v.o + off;
+  return (p >= v.ia && p + 12u <= v.ib) ? lds12(in + p) : load12_any(sp + off, v.lo, v.hi);
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 c, uint32_t k) {
+  return k < 2 ? (k == 0 ? c.x : c.y) : (k == 2 ? c.z : c.w);
+}
+
+__device__ __forceinline__ uint32_t byte_of(uint4 c, uint32_t k) {
+  return (word_of(c, k >> 2) >> (8u * (k & 3u))) & 0xFFu;
+}
+
+// Encodes one tile (Algorithm 1 per 12-byte unit) straight to global memory
+// in aligned 16-byte stores; the message's last tile also codes the partial
+// group with its padding.
+//  - Output start d word-aligned (d mod 16 = 4q, always so for padded
+//    output at a word-aligned base): the lane of aligned chunk c writes the
+//    16 characters at d - 4q + 16c, which encode tile bytes
+//    [12c - 3q, 12c - 3q + 12). With q > 0, chunk 0 keeps the first 4 - q
+//    words of unit 0's characters and chunk nu the last q words of unit
+//    nu - 1's.
+//  - Otherwise (d mod 4 != 0): lanes code units, and the lane of unit u
+//    builds aligned chunk u from unit u - 1 (the previous lane, or the
+//    previous row's last lane) and unit u; the ends go out as bytes.
+__device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in,
+                                            const uint8_t* T, uint32_t lane, uint32_t flags) {
+  const uint32_t nu = v.len / 12u;
+  const uint8_t* sp = v.msrc + v.t0;
+  uint8_t* dp = v.dst;
+  const uint32_t o2 = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15u);
+  uint8_t* abase = dp - o2;  // 16-byte aligned
+  if ((o2 & 3u) == 0) {
+    const uint32_t q = o2 >> 2;
+    const uint32_t nc = nu == 0 ? 0u : (q ? nu + 1u : nu);
+#pragma unroll 2
+    for (uint32_t c = lane; c < nc; c += 32u) {
+      const bool head = q && c == 0, tail = q && c == nu;
+      const uint32_t off = head ? 0u : (tail ? 12u * (nu - 1u) : 12u * c - 3u * q);
+      const uint3 w = enc_load(v, in, sp, off);
+      const uint4 e = enc_unit(w.x, w.y, w.z, T);
+      if (!head && !tail) {
+        st_global_v4_cs(abase + 16u * c, e);
+      } else {
+        uint32_t* wd = reinterpret_cast<uint32_t*>(head ? dp : dp + 16u * nu - 4u * q);
+        const uint32_t k0 = head ? 0u : 4u - q, nk = head ? 4u - q : q;
+        for (uint32_t k = 0; k < nk; ++k) wd[k] = word_of(e, k0 + k);
+      }
     }
-    const uint32_t u0 = base + (tid & ~31u);
-    if (u0 < nu) store12_warp(m.out + t0 / 4 * 3 + 12 * u0, o, lane, min(32u, nu - u0));
+  } else {
+    uint4 carry = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t base = 0; base < nu; base += 32u) {
+      const uint32_t u = base + lane;
+      uint4 c = make_uint4(0u, 0u, 0u, 0u);
+      if (u < nu) {
+        const uint3 w = enc_load(v, in, sp, 12u * u);
+        c = enc_unit(w.x, w.y, w.z, T);
+      }
+      uint4 prev;
+      prev.x = __shfl_up_sync(0xFFFFFFFFu, c.x, 1);
+      prev.y = __shfl_up_sync(0xFFFFFFFFu, c.y, 1);
+      prev.z = __shfl_up_sync(0xFFFFFFFFu, c.z, 1);
+      prev.w = __shfl_up_sync(0xFFFFFFFFu, c.w, 1);
+      if (lane == 0) prev = carry;
+      if (u < nu) {
+        if (u > 0) {
+          st_global_v4_cs(abase + 16u * u, realign16(prev, c, 16u - o2));
+        } else {
+          for (uint32_t k = 0; k < 16u - o2; ++k) dp[k] = (uint8_t)byte_of(c, k);
+        }
+        if (u == nu - 1) {
+          uint8_t* t = dp + 16u * nu - o2;
+          for (uint32_t k = 0; k < o2; ++k) t[k] = (uint8_t)byte_of(c, 16u - o2 + k);
+        }
+      }
+      carry.x = __shfl_sync(0xFFFFFFFFu, c.x, 31);
+      carry.y = __shfl_sync(0xFFFFFFFFu, c.y, 31);
+      carry.z = __shfl_sync(0xFFFFFFFFu, c.z, 31);
+      carry.w = __shfl_sync(0xFFFFFFFFu, c.w, 31);
+    }
+  }
+  const uint32_t rest = v.len - 12u * nu;
+  const uint32_t ng = (rest + 2u) / 3u;
+  if (lane < ng) {
+    const uint8_t* p = sp + 12u * nu + 3u * lane;
+    const uint32_t cnt = min(3u, rest - 3u * lane);
+    const uint32_t b0 = p[0], b1 = cnt > 1 ? p[1] : 0u, b2 = cnt > 2 ? p[2] : 0u;
+    store_tail_group(dp + 16u * nu + 4u * lane, enc_tail_group(b0, b1, b2, cnt, T), cnt, flags);
+  }
+}
+
+// Characters of decode unit u of a tile, from the stage or global memory.
+__device__ __forceinline__ uint4 dec_load(const TileView& v, const uint8_t* in, uint32_t u) {
+  const uint32_t p = v.o + 16u * u;
+  if (p >= v.ia && p + 16u <= v.ib) {
+    const uint4* q = reinterpret_cast<const uint4*>(in + (p & ~15u));
+    return v.o ? realign16(q[0], q[1], v.o) : q[0];
+  }
+  return load16_any(v.msrc + v.t0 + 16u * u, v.lo, v.hi);
+}
+
+// Stages a row of decoded units (12 bytes each at o2 + 12u): word stores
+// when o2 is word-aligned, else aligned words whose first one takes the
+// last bytes of unit u - 1 (the previous lane, or `carry` from the previous
+// row). Every lane of the warp calls it.
+__device__ __forceinline__ void dec_store_row(uint8_t* out, uint32_t o2, uint32_t u, uint32_t nu,
+                                              uint3 o, uint32_t& carry, uint32_t lane) {
+  const uint32_t r2 = o2 & 3u;
+  if (r2 == 0) {
+    if (u < nu) {
+      uint32_t* wq = reinterpret_cast<uint32_t*>(out + o2 + 12u * u);
+      wq[0] = o.x;
+      wq[1] = o.y;
+      wq[2] = o.z;
+    }
+    return;
+  }
+  uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, o.z, 1);
+  if (lane == 0) prev = carry;
+  if (u < nu) {
+    uint32_t* wq = reinterpret_cast<uint32_t*>(out + ((o2 + 12u * u) & ~3u));
+    const uint32_t sh = 8u * (4u - r2);
+    wq[0] = __funnelshift_r(prev, o.x, sh);
+    wq[1] = __funnelshift_r(o.x, o.y, sh);
+    wq[2] = __funnelshift_r(o.y, o.z, sh);
+    if (u == nu - 1) wq[3] = __funnelshift_r(o.z, o.z, sh);
+  }
+  carry = __shfl_sync(0xFFFFFFFFu, o.z, 31);
+}
+
+// Decodes one tile (Algorithm 2 per 16-character unit; whole quads after
+// the last unit and, in the tile holding it, the message's final group go
+// straight to global memory).
+__device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in, uint8_t* out,
+                                            const uint8_t* D, unsigned long long* fb,
+                                            int64_t* outlen_j, uint32_t lane, uint32_t flags) {
+  const uint64_t mlen = (uint64_t)v.mlen;
+  const uint64_t body_end = decode_body_end(mlen);
+  const uint64_t t0 = (uint64_t)v.t0;
+  const uint32_t body = body_end > t0 ? (uint32_t)tmin<uint64_t>(v.len, body_end - t0) : 0u;
+  const uint32_t nu = body / 16u;
+  uint8_t* dp = v.dst;
+  const uint32_t o2 = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15u);
+  unsigned long long bad = ~0ull;
+  uint32_t carry = 0;  // last word of the previous row's last unit
+  // Two rows per pass, as in encode_tile.
+  for (uint32_t base = 0; base < nu; base += 64u) {
+    const uint32_t ua = base + lane, ub = ua + 32u;
+    const bool two = base + 32u < nu;
+    uint4 wa = make_uint4(0u, 0u, 0u, 0u), wb = wa;
+    if (ua < nu) wa = dec_load(v, in, ua);
+    if (two && ub < nu) wb = dec_load(v, in, ub);
+    uint32_t ea = 0, eb = 0;
+    const uint3 oa = dec_unit(wa, D, ea);
+    uint3 ob = make_uint3(0u, 0u, 0u);
+    if (two) ob = dec_unit(wb, D, eb);
+    if (((ea | eb) & kBadFlag) && bad == ~0ull) {
+      if ((ea & kBadFlag) && ua < nu) {
+        bad = t0 + 16u * ua + dec_unit_first_bad(wa, D);
+      } else if ((eb & kBadFlag) && ub < nu) {
+        bad = t0 + 16u * ub + dec_unit_first_bad(wb, D);
+      }
+    }
+    dec_store_row(out, o2, ua, nu, oa, carry, lane);
+    if (two) dec_store_row(out, o2, ub, nu, ob, carry, lane);
   }
   warp_min_to(fb, bad);
-  const uint32_t nq = (body - 16 * nu) / 4;
-  if (tid < nq) {
-    const uint64_t idx = t0 + 16 * nu + 4 * tid;
-    const uint8_t* p = m.src + idx;
+  const uint32_t nq = (body - 16u * nu) / 4u;
+  if (lane < nq) {
+    const uint64_t idx = t0 + 16u * nu + 4u * lane;
+    const uint8_t* p = v.msrc + idx;
     const uint32_t x = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
                        ((uint32_t)p[3] << 24);
     uint32_t err = 0;
-    const uint32_t v = dec_quad(x, D, err);
+    const uint32_t val = dec_quad(x, D, err);
     if (err & kBadFlag) {
       for (uint32_t q = 0; q < 4; ++q)
         if (D[(x >> (8 * q)) & 0xFFu] & kBadFlag) {
@@ -277,58 +480,121 @@ __device__ __forceinline__ void decode_tile(const Msg& m, uint64_t t0, int64_t t
           break;
         }
     } else {
-      uint8_t* o = m.out + idx / 4 * 3;
-      o[0] = (uint8_t)(v >> 16);
-      o[1] = (uint8_t)(v >> 8);
-      o[2] = (uint8_t)v;
+      uint8_t* w = v.mout + idx / 4 * 3;
+      w[0] = (uint8_t)(val >> 16);
+      w[1] = (uint8_t)(val >> 8);
+      w[2] = (uint8_t)val;
     }
   }
-  if (tid == NT - 1 && body_end >= t0 && body_end < t0 + len)
-    *outlen_j = dec_final_group(m.src, mlen, body_end, m.out, D, fb, flags);
+  if (lane == 31 && body_end >= t0 && body_end < t0 + v.len)
+    *outlen_j = dec_final_group(v.msrc, mlen, body_end, v.mout, D, fb, flags);
+  fence_proxy_async_smem();
+  __syncwarp();
+  copy_out(dp, 12u * nu, out, lane);
 }
 
-// Persistent tile walk: CTA b owns tiles [b*T/G, (b+1)*T/G) of the
-// T = tile_off[nmsg] tiles, in order.
-template <int NT, class Msgs>
-__global__ void __launch_bounds__(NT)
-    k_batch_encode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
-                   uint32_t flags) {
-  __shared__ uint8_t T[64];
-  init_tables(T, nullptr, flags & kFlagUrl);
-  const int64_t total = tile_off[nmsg];
-  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-  int64_t t = (int64_t)blockIdx.x * per;
-  const int64_t t_end = min(total, t + per);
-  if (t >= t_end) return;
-  Msgs ms = msgs;
-  ms.prepare(nmsg);
-  int64_t j = owner_of(tile_off, nmsg, t);
-  for (; t < t_end; ++t) {
-    while (__ldg(tile_off + j + 1) <= t) ++j;
-    encode_tile<NT>(ms.get(j), (t - __ldg(tile_off + j)) * tile, tile, T, flags);
-  }
+// Shared memory of a warp: `stages` input stages, and (decode) two output
+// buffers, used by alternate tiles.
+__host__ __device__ __forceinline__ uint32_t stage_in_bytes(int64_t tile) {
+  return (uint32_t)tile + 32u;
+}
+__host__ __device__ __forceinline__ int64_t out_tile_bytes(int decode, int64_t tile) {
+  return decode ? tile / 4 * 3 : tile / 3 * 4;
+}
+__host__ __device__ __forceinline__ uint32_t warp_smem_bytes(int decode, int64_t tile,
+                                                             uint32_t stages) {
+  return stages * stage_in_bytes(tile) + (decode ? 2u * ((uint32_t)out_tile_bytes(1, tile) + 32u) : 0u);
 }
 
-template <int NT, class Msgs>
+// The persistent kernel of both directions: warp w of the grid's G warps
+// owns tiles [w*T/G, (w+1)*T/G) of the T = tile_off[nmsg] tiles, in order.
+// Lane 0 of the warp computes each tile's view once, when it issues the
+// tile's copy, and leaves it beside the stage.
+template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_decode(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
-                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
-                   uint32_t flags) {
-  __shared__ uint8_t D[256];
-  init_tables(nullptr, D, flags & kFlagUrl);
-  const int64_t total = tile_off[nmsg];
-  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-  int64_t t = (int64_t)blockIdx.x * per;
-  const int64_t t_end = min(total, t + per);
-  if (t >= t_end) return;
+    k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
+                 uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
+                 uint32_t flags) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint8_t table[DECODE ? 256 : 64];
+  __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
+  __shared__ TileView meta[NT / 32][kMaxBatchStages];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t S = stages;
+  if (lane == 0) {
+    for (uint32_t s = 0; s < S; ++s) mbar_init(&full[warp][s], 1);
+    fence_mbar_init();
+  }
+  if (DECODE) {
+    init_tables(nullptr, table, flags & kFlagUrl);
+  } else {
+    init_tables(table, nullptr, flags & kFlagUrl);
+  }
+  const int64_t out_tile = out_tile_bytes(DECODE, tile);
+  const uint32_t in_b = stage_in_bytes(tile), out_b = (uint32_t)out_tile + 32u;
+  uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, tile, S);
+  uint8_t* obase = wbase + S * in_b;  // decode: the two output buffers
+
+  const int64_t total = __ldg(tile_off + nmsg);
+  const int64_t nw = (int64_t)gridDim.x * (NT / 32);
+  const int64_t per = (total + nw - 1) / nw;
+  const int64_t t_begin = ((int64_t)blockIdx.x * (NT / 32) + warp) * per;
+  const int64_t t_end = tmin<int64_t>(total, t_begin + per);
+  if (t_begin >= t_end) return;
   Msgs ms = msgs;
   ms.prepare(nmsg);
-  int64_t j = owner_of(tile_off, nmsg, t);
-  for (; t < t_end; ++t) {
-    while (__ldg(tile_off + j + 1) <= t) ++j;
-    decode_tile<NT>(ms.get(j), (uint64_t)(t - __ldg(tile_off + j)) * tile, tile, D,
-                    reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j, flags);
+  if (lane == 0) {
+    int64_t ji = owner_of(tile_off, nmsg, t_begin);
+    for (uint32_t s = 0; s < S && t_begin + s < t_end; ++s) {
+      meta[warp][s] = tile_view(ms, tile_off, t_begin + s, ji, tile, out_tile);
+      issue_tile(meta[warp][s], wbase + s * in_b, &full[warp][s]);
+    }
   }
+
+  bool timed_out = false;
+  uint32_t s = 0, phase = 0;
+  int64_t t = t_begin;
+  for (; t < t_end; ++t) {
+    uint8_t* in = wbase + s * in_b;
+    const bool ok = mbar_wait_backoff(&full[warp][s], phase);
+    if (__any_sync(0xFFFFFFFFu, !ok)) {
+      timed_out = true;
+      break;
+    }
+    const TileView v = meta[warp][s];
+    if (DECODE) {
+      // the bulk store that last read this output buffer is done with it
+      if (lane == 0 && t - t_begin >= 2) bulk_wait_read(1);
+      __syncwarp();
+      decode_tile(v, in, obase + ((uint32_t)(t - t_begin) & 1u) * out_b, table,
+                  reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j, lane, flags);
+    } else {
+      encode_tile(v, in, table, lane, flags);
+      fence_proxy_async_smem();  // the stage's reads come before its next copy
+      __syncwarp();
+    }
+    if (lane == 0 && t + S < t_end) {
+      int64_t ji = v.j;
+      meta[warp][s] = tile_view(ms, tile_off, t + S, ji, tile, out_tile);
+      issue_tile(meta[warp][s], in, &full[warp][s]);
+    }
+    if (++s == S) {
+      s = 0;
+      phase ^= 1u;
+    }
+  }
+  if (timed_out && lane == 0) {
+    atomicOr(&g_batch_fault, 1u);
+    // wait (bounded) for the copies still in flight into this warp's stages
+    for (uint32_t i = 0; i < S && t + i < t_end; ++i) {
+      mbar_wait_bounded(&full[warp][s], phase, 500000000ull);
+      if (++s == S) {
+        s = 0;
+        phase ^= 1u;
+      }
+    }
+  }
+  if (DECODE && lane == 0) bulk_wait_all();
 }
 
 // Per-message status: first bad character wins, then the length rule, then
@@ -358,6 +624,10 @@ __global__ void k_batch_decode_init(int64_t nmsg, int64_t* __restrict__ first_ba
 }
 
 // ------------------------------------------------------------------ host
+size_t batch_smem_bytes(int decode, const BatchConfig& c) {
+  return (size_t)(c.threads / 32) * warp_smem_bytes(decode, c.tile, (uint32_t)c.stages);
+}
+
 size_t batch_scratch_bytes(int64_t nmsg) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
   return (size_t)(nmsg + 1) * 8 + (size_t)std::max<int64_t>(nparts, 1) * 16;
@@ -388,14 +658,24 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
                         int32_t* status, int64_t* first_bad, int64_t* outlen,
                         const BatchConfig& cfg, const DeviceInfo* di, uint32_t flags,
                         cudaStream_t stream) {
-  const int grid = di->sm_count * cfg.blocks_per_sm;
+  const size_t smem = batch_smem_bytes(decode, cfg);
+  const void* kernel = decode ? reinterpret_cast<const void*>(k_batch_code<NT, 1, Msgs>)
+                              : reinterpret_cast<const void*>(k_batch_code<NT, 0, Msgs>);
+  int fit = 0;
+  cudaError_t e = kernel_prepare(kernel, smem, NT, &fit);
+  if (e != cudaSuccess) return e;
+  if (fit < 1) return cudaErrorInvalidConfiguration;
+  const int bps = cfg.blocks_per_sm > 0 ? std::min(fit, cfg.blocks_per_sm) : fit;
+  const int grid = di->sm_count * bps;
+  const uint32_t stages = (uint32_t)cfg.stages;
   if (!decode) {
-    k_batch_encode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile, flags);
+    k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
+                                                          nullptr, nullptr, flags);
     return cudaGetLastError();
   }
-  k_batch_decode<NT, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, cfg.tile, first_bad,
-                                                    outlen, flags);
-  cudaError_t e = cudaGetLastError();
+  k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
+                                                        first_bad, outlen, flags);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
   k_batch_decode_finish<Msgs><<<(unsigned)blocks, 256, 0, stream>>>(msgs, nmsg, status, first_bad,

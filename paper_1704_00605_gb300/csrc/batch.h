@@ -11,9 +11,10 @@ namespace gb64 {
 // Shape of a batched launch.
 struct BatchConfig {
   int threads;        // 128, 256 or 512 threads per CTA
-  int64_t tile;       // input bytes (encode, multiple of 48) or characters
-                      // (decode, multiple of 64) per tile
-  int blocks_per_sm;  // persistent CTAs per SM
+  int64_t tile;       // input bytes (encode, multiple of 384) or characters
+                      // (decode, multiple of 512) per warp tile
+  int blocks_per_sm;  // persistent CTAs per SM at most (0: as many as fit)
+  int stages = 4;     // input stages per warp (2..6)
 };
 
 struct BatchArgs {
@@ -67,8 +68,17 @@ cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
 // Offsets + the persistent tile kernel (+ the decode finish kernel).
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);
 
+// Largest dynamic shared memory a valid batch shape may ask for: the
+// opt-in limit of a CTA on sm_103 (227 KiB) less the kernel's static tables,
+// barriers and tile views. A launch still checks the device it runs on.
+constexpr size_t kBatchSmemLimit = 227 * 1024 - 8 * 1024;
+
+// Dynamic shared memory of a batched launch: per warp, `stages` input
+// stages of a tile (and, decoding, two output buffers).
+size_t batch_smem_bytes(int decode, const BatchConfig& c);
+
 // Valid shapes and the defaults used when the tuner has no entry.
 bool batch_config_valid(int decode, const BatchConfig& c);
-BatchConfig default_batch_config(int decode);
+BatchConfig default_batch_config(int decode, int64_t mean_len = -1);
 
 }  // namespace gb64

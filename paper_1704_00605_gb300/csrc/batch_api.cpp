@@ -10,15 +10,20 @@ namespace gb64 {
 
 bool batch_config_valid(int decode, const BatchConfig& c) {
   if (c.threads != 128 && c.threads != 256 && c.threads != 512) return false;
-  if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return false;
-  if (c.tile < 64 || c.tile > (1 << 24)) return false;
-  return decode ? (c.tile % 64 == 0) : (c.tile % 48 == 0);
+  if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) return false;
+  if (c.stages < 2 || c.stages > 6) return false;
+  const int64_t row = decode ? 512 : 384;  // one unit per lane of a warp
+  if (c.tile < row || c.tile > 16 * row || c.tile % row) return false;
+  return batch_smem_bytes(decode, c) <= kBatchSmemLimit;
 }
 
-// Fastest shapes measured on GB300 for the 100,000-message workload (mean
-// message length 6.6 KiB): small CTAs, many per SM.
-BatchConfig default_batch_config(int decode) {
-  return decode ? BatchConfig{128, 8192, 8} : BatchConfig{128, 12288, 16};
+// Shapes measured fastest on GB300 with the tuner: mean message length
+// below 1 KiB (262,144 messages of 256 B) and above (100,000 messages of
+// 6.3 KiB on average, and 256 of 1 MiB). mean_len < 0: unknown.
+BatchConfig default_batch_config(int decode, int64_t mean_len) {
+  const bool small = mean_len >= 0 && mean_len < 1024;
+  if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{256, 2048, 0, 3};
+  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 3072, 0, 2};
 }
 
 namespace {

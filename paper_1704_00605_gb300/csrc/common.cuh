@@ -111,6 +111,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// As mbar_wait_bounded, but sleeping briefly between polls, so that warps
+// waiting for their next tile leave the issue slots to the warps computing.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t i = 0;; ++i) {
+    __nanosleep(64);
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15u) == 15u && global_timer_ns() - t0 > limit_ns) return false;
+  }
+}
+
 // 1-D bulk copy global -> shared, completing `bytes` transactions on bar.
 // Both addresses and bytes must be multiples of 16.
 __device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* gsrc, uint32_t bytes,
@@ -141,6 +154,17 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 // All committed bulk stores are complete (written to global memory).
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// At most n (0..3) of the committed bulk-store groups still read shared
+// memory.
+__device__ __forceinline__ void bulk_wait_read(uint32_t n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+  }
 }
 
 // Orders this thread's generic-proxy shared-memory accesses with later
@@ -340,6 +364,33 @@ __device__ __forceinline__ void store4_any(uint8_t* p, uint32_t w) {
     p[2] = (uint8_t)(w >> 16);
     p[3] = (uint8_t)(w >> 24);
   }
+}
+
+// Bytes [sft, sft + 16) of the 32 bytes lo || hi (lo first, little-endian
+// words), for sft in 0..15; sft is the same in every lane of a warp.
+__device__ __forceinline__ uint4 realign16(uint4 lo, uint4 hi, uint32_t sft) {
+  const uint32_t sh = 8u * (sft & 3u);
+  uint32_t a, b, c, d, e;
+  switch (sft >> 2) {
+    case 0: a = lo.x; b = lo.y; c = lo.z; d = lo.w; e = hi.x; break;
+    case 1: a = lo.y; b = lo.z; c = lo.w; d = hi.x; e = hi.y; break;
+    case 2: a = lo.z; b = lo.w; c = hi.x; d = hi.y; e = hi.z; break;
+    default: a = lo.w; b = hi.x; c = hi.y; d = hi.z; e = hi.w; break;
+  }
+  return make_uint4(__funnelshift_r(a, b, sh), __funnelshift_r(b, c, sh), __funnelshift_r(c, d, sh),
+                    __funnelshift_r(d, e, sh));
+}
+
+// Bytes p[0..11] of shared memory as three little-endian words, read as
+// aligned words (one more when p is not word-aligned).
+__device__ __forceinline__ uint3 lds12(const uint8_t* p) {
+  const uint32_t r = (uint32_t)(reinterpret_cast<uintptr_t>(p) & 3u);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(p - r);
+  if (r == 0) return make_uint3(q[0], q[1], q[2]);
+  const uint32_t sh = 8u * r;
+  const uint32_t q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+  return make_uint3(__funnelshift_r(q0, q1, sh), __funnelshift_r(q1, q2, sh),
+                    __funnelshift_r(q2, q3, sh));
 }
 
 // Writes the final group's characters: 4 with padding, or cnt + 1 (2 or 3)

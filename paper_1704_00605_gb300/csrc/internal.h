@@ -41,6 +41,12 @@ TileConfig default_encode_config(uint64_t n);
 TileConfig default_decode_config(uint64_t m);
 size_t single_smem_bytes(int decode, const TileConfig& c);
 
+// Raises the kernel's dynamic shared-memory limit to the device maximum (once
+// per device and kernel) and returns how many CTAs of `threads` threads and
+// smem_bytes of dynamic shared memory fit per SM (cached). Fails with
+// cudaErrorInvalidValue when smem_bytes does not fit the device.
+cudaError_t kernel_prepare(const void* kernel, size_t smem_bytes, int threads, int* blocks_per_sm);
+
 // Single-buffer encode of n >= 1 bytes; picks the TMA kernel when src and
 // dst are 16-byte aligned, else the generic one.
 cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStream_t stream,

@@ -409,14 +409,11 @@ size_t single_smem_bytes(int decode, const TileConfig& c) {
   return (size_t)c.stages * tile + (decode ? 2 * (size_t)c.threads * c.upt * 12 : 0);
 }
 
-namespace {
-
 // Raises the kernel's dynamic shared-memory limit to the device maximum
 // (once per device and kernel: the limit belongs to the kernel, not to one
 // launch) and returns how many CTAs of smem_bytes fit per SM (cached per
 // device, kernel, size and block size, so small launches pay it once).
-template <typename K>
-cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm) {
+cudaError_t kernel_prepare(const void* kernel, size_t smem_bytes, int threads, int* blocks_per_sm) {
   struct Key {
     int device;
     const void* kernel;
@@ -429,7 +426,7 @@ cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
-  const void* kp = reinterpret_cast<const void*>(kernel);
+  const void* kp = kernel;
   std::lock_guard<std::mutex> g(mu);
   bool raised = false;
   for (const Key& k : cache) {
@@ -460,6 +457,8 @@ cudaError_t prepare(K kernel, size_t smem_bytes, int threads, int* blocks_per_sm
   return cudaSuccess;
 }
 
+namespace {
+
 bool valid_config(const TileConfig& c) {
   return (c.threads == 128 || c.threads == 256 || c.threads == 512) && c.upt >= 1 &&
          c.upt <= 16 && c.stages >= 2 && c.stages <= kMaxStages && c.blocks_per_sm >= 0;
@@ -484,7 +483,7 @@ cudaError_t launch_encode_nt(const uint8_t* src, uint64_t n, uint8_t* dst, cudaS
                   : f == kFlagNoPad               ? k_encode_tma<NT, kFlagNoPad>
                                                   : k_encode_tma<NT, kFlagUrl | kFlagNoPad>;
     int bps = 0;
-    cudaError_t e = prepare(kernel, smem, NT, &bps);
+    cudaError_t e = kernel_prepare(reinterpret_cast<const void*>(kernel), smem, NT, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = (n + tile_in - 1) / tile_in;
@@ -513,7 +512,8 @@ cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileC
     const uint64_t tile_o = (uint64_t)NT * cfg.upt * 12u;
     const size_t smem = (size_t)cfg.stages * tile_c + 2 * tile_o;
     int bps = 0;
-    cudaError_t e = prepare(k_decode_tma<NT, DEVLEN>, smem, NT, &bps);
+    cudaError_t e =
+        kernel_prepare(reinterpret_cast<const void*>(k_decode_tma<NT, DEVLEN>), smem, NT, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = std::max<uint64_t>(1, (a.m + tile_c - 1) / tile_c);

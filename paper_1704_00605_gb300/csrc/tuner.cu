@@ -57,14 +57,19 @@ void load_env_once_locked() {
   if (const char* p = getenv("GB64_TUNE_FILE")) load_file_locked(p);
 }
 
+BatchConfig batch_config_of(const b64_shape& s) {
+  BatchConfig c{s.threads, s.tile, s.blocks_per_sm};
+  c.stages = s.stages ? s.stages : 4;
+  return c;
+}
+
 bool shape_valid(int kind, const b64_shape& s) {
   if (kind == kSingleEncode || kind == kSingleDecode) {
     TileConfig c{s.threads, s.units_per_thread, s.stages, s.blocks_per_sm};
     return (c.threads == 128 || c.threads == 256 || c.threads == 512) && c.upt >= 1 &&
            c.upt <= 16 && c.stages >= 2 && c.stages <= 8 && c.blocks_per_sm >= 0;
   }
-  BatchConfig c{s.threads, s.tile, s.blocks_per_sm};
-  return batch_config_valid(kind == kBatchDecode, c);
+  return batch_config_valid(kind == kBatchDecode, batch_config_of(s));
 }
 
 __global__ void k_fill_random(uint8_t* p, uint64_t n, uint64_t seed) {
@@ -137,15 +142,12 @@ std::vector<b64_shape> single_candidates(int decode, const DeviceInfo* di) {
 
 std::vector<b64_shape> batch_candidates(int decode) {
   std::vector<b64_shape> out;
-  const int unit = decode ? 16 : 12;
-  for (int threads : {128, 256, 512})
-    for (int k : {1, 2, 4, 8})
-      for (int bps : {4, 8, 16}) {
-        if (threads * bps > 2048) continue;
-        int64_t tile = (int64_t)threads * unit * k;
-        const int64_t q = decode ? 64 : 48;
-        tile = (tile + q - 1) / q * q;
-        out.push_back(b64_shape{threads, 0, 0, bps, tile, 0.f});
+  const int64_t row = decode ? 512 : 384;
+  for (int threads : {128, 256})
+    for (int rows : {2, 4, 8})
+      for (int stages : {2, 3, 4, 6}) {
+        const b64_shape s{threads, 0, stages, 0, row * rows, 0.f};
+        if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
       }
   return out;
 }
@@ -186,8 +188,8 @@ BatchConfig tuned_batch_config(int decode, int64_t nmsg, int64_t total_bytes) {
   load_env_once_locked();
   const int kind = decode ? kBatchDecode : kBatchEncode;
   const Entry& e = g_table[kind][bucket_of(kind, total_bytes, nmsg)];
-  if (e.set) return BatchConfig{e.s.threads, e.s.tile, e.s.blocks_per_sm};
-  return default_batch_config(decode);
+  if (e.set) return batch_config_of(e.s);
+  return default_batch_config(decode, (total_bytes >= 0 && nmsg > 0) ? total_bytes / nmsg : -1);
 }
 
 }  // namespace gb64
@@ -209,7 +211,7 @@ int b64_shape_get(int kind, int64_t total, int64_t nmsg, b64_shape* out) {
                      (int64_t)c.threads * c.upt * unit, 0.f};
   } else {
     const BatchConfig c = tuned_batch_config(kind == kBatchDecode, nmsg, total);
-    *out = b64_shape{c.threads, 0, 0, c.blocks_per_sm, c.tile, 0.f};
+    *out = b64_shape{c.threads, 0, c.stages, c.blocks_per_sm, c.tile, 0.f};
   }
   return B64_OK;
 }
@@ -347,7 +349,7 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
       ea.src = raw;
       ea.dst = enc;
       ea.out_off = enc_off;
-      e = batch_launch(ea, default_batch_config(0));
+      e = batch_launch(ea, default_batch_config(0, (int64_t)raw_n / nmsg));
     } else {
       e = launch_encode(raw, raw_n, enc, stream, default_encode_config(raw_n));
     }
@@ -367,7 +369,7 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
         a.in_off = decode ? enc_off : in_off;
         a.dst = decode ? dec : enc;
         a.out_off = decode ? out_off : enc_off;
-        return batch_launch(a, BatchConfig{s.threads, s.tile, s.blocks_per_sm});
+        return batch_launch(a, batch_config_of(s));
       }
       const TileConfig c{s.threads, s.units_per_thread, s.stages, s.blocks_per_sm};
       if (!decode) return launch_encode(raw, raw_n, enc, stream, c);

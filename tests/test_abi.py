@@ -127,11 +127,19 @@ def test_shape_table_host_side(g, tmp_path):
         g.b64_shape_set(g.B64_KIND_ENCODE, 1 << 20, threads=100)
     with pytest.raises(g.Gb64Error):
         g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=256, tile=1000)
-    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=512, tile=512 * 16, blocks_per_sm=4)
+    with pytest.raises(g.Gb64Error):  # not a whole number of warp rows (512 characters)
+        g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=128, tile=768)
+    with pytest.raises(g.Gb64Error):  # 16 warps x 4 stages x 14 KiB: more shared memory than a CTA has
+        g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=512, tile=8192, stages=4)
+    with pytest.raises(g.Gb64Error):
+        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=128, tile=1536, stages=7)
+    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=512, tile=1024, stages=2,
+                    blocks_per_sm=4)
+    assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["stages"] == 2
     path = str(tmp_path / "shapes.txt")
     g.b64_tune_save(path)
     text = open(path).read()
     assert "512" in text and "128" in text
-    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=256, tile=256 * 16, blocks_per_sm=8)
+    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=256, tile=2048, blocks_per_sm=8)
     g.b64_tune_load(path)
     assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["threads"] == 512
