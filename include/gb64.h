@@ -151,9 +151,15 @@ enum {
  * fit). Batch kinds use threads, tile (input bytes per warp tile, a
  * multiple of 384 up to 6144, or characters, a multiple of 512 up to
  * 8192), stages (input stages per warp, 2..6; 0 = 4) and blocks_per_sm
- * (0 = as many as fit); the shape's shared memory, threads / 32 * (stages *
- * (tile + 32) + (decode only) 2 * (3 * tile / 4 + 32)) bytes, must stay
- * within 219 KiB. ms is a measured time. */
+ * (0 = as many as fit) of the per-warp tile kernels; the shape's shared
+ * memory, threads / 32 * (stages * (tile + 32) + (decode only) 2 *
+ * (3 * tile / 4 + 32)) bytes, must stay within 219 KiB. For batch kinds
+ * units_per_thread selects the kernel of packed batches whose input
+ * (decode) or output (padded encode) starts on a 16-byte boundary: 0 = the
+ * flat whole-batch kernels when the mean message length is short (decided
+ * on the device), 1 = always the flat kernels, 2 = always the per-warp
+ * tile kernels; other batches always take the per-warp kernels. ms is a
+ * measured time. */
 typedef struct {
   int32_t threads;
   int32_t units_per_thread;

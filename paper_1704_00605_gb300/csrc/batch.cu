@@ -197,6 +197,10 @@ struct PackedMsgs {
     return __ldg(in_off + j + 1) - __ldg(in_off + j);
   }
   __device__ __forceinline__ void prepare(int64_t nmsg) { src_hi = src + __ldg(in_off + nmsg); }
+  // mean message length (the batch's bytes over its messages)
+  __device__ __forceinline__ int64_t mean_len(int64_t nmsg) const {
+    return nmsg > 0 ? __ldg(in_off + nmsg) / nmsg : 0;
+  }
 };
 
 // Messages anywhere in device memory, one descriptor each (the server).
@@ -209,6 +213,7 @@ struct DescMsgs {
   }
   __device__ __forceinline__ int64_t len(int64_t j) const { return desc[j].len; }
   __device__ __forceinline__ void prepare(int64_t) {}
+  __device__ __forceinline__ int64_t mean_len(int64_t) const { return INT64_MAX; }
 };
 
 // ------------------------------------------------------ warp pipeline
@@ -514,7 +519,9 @@ template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
     k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
                  uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
-                 uint32_t flags) {
+                 uint32_t flags, int64_t min_mean_len) {
+  // a packed batch of shorter messages on average is the flat kernel's
+  if (min_mean_len > 0 && msgs.mean_len(nmsg) < min_mean_len) return;
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
@@ -657,7 +664,7 @@ template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                         int32_t* status, int64_t* first_bad, int64_t* outlen,
                         const BatchConfig& cfg, const DeviceInfo* di, uint32_t flags,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int64_t min_mean_len) {
   const size_t smem = batch_smem_bytes(decode, cfg);
   const void* kernel = decode ? reinterpret_cast<const void*>(k_batch_code<NT, 1, Msgs>)
                               : reinterpret_cast<const void*>(k_batch_code<NT, 0, Msgs>);
@@ -670,11 +677,11 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const uint32_t stages = (uint32_t)cfg.stages;
   if (!decode) {
     k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                          nullptr, nullptr, flags);
+                                                          nullptr, nullptr, flags, min_mean_len);
     return cudaGetLastError();
   }
   k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                        first_bad, outlen, flags);
+                                                        first_bad, outlen, flags, min_mean_len);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
@@ -686,20 +693,21 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
 template <class Msgs>
 cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                             int32_t* status, int64_t* first_bad, int64_t* outlen,
-                            const BatchConfig& cfg, uint32_t flags, cudaStream_t stream) {
+                            const BatchConfig& cfg, uint32_t flags, cudaStream_t stream,
+                            int64_t min_mean_len = 0) {
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
     case 128:
       return launch_work<128>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream);
+                              flags, stream, min_mean_len);
     case 512:
       return launch_work<512>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream);
+                              flags, stream, min_mean_len);
     default:
       return launch_work<256>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream);
+                              flags, stream, min_mean_len);
   }
 }
 }  // namespace
@@ -725,6 +733,26 @@ cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
   if (e != cudaSuccess) return e;
   // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
   PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
+  if (cfg.flat != 2 && flat_eligible(a.decode, a.src, a.dst, a.flags)) {
+    if (cfg.flat == 1) {
+      e = flat_launch(a.decode, a.src, a.in_off, a.dst, a.out_off, a.nmsg, a.first_bad, a.outlen,
+                      default_flat_config(a.decode), a.flags, a.stream);
+      if (e != cudaSuccess || !a.decode) return e;
+      const int64_t blocks = std::max<int64_t>(1, (a.nmsg + 255) / 256);
+      k_batch_decode_finish<PackedMsgs><<<(unsigned)blocks, 256, 0, a.stream>>>(
+          msgs, a.nmsg, a.status, a.first_bad, a.outlen, a.flags);
+      return cudaGetLastError();
+    }
+    // Both kernels are enqueued; each reads the batch's mean message length
+    // on the device and only one of them codes: the flat kernel below the
+    // threshold, the per-warp tile kernel from it on (no host read needed).
+    const int64_t threshold = flat_mean_len_threshold(a.decode);
+    e = flat_launch(a.decode, a.src, a.in_off, a.dst, a.out_off, a.nmsg, a.first_bad, a.outlen,
+                    default_flat_config(a.decode), a.flags, a.stream, threshold);
+    if (e != cudaSuccess) return e;
+    return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen,
+                           cfg, a.flags, a.stream, threshold);
+  }
   return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen, cfg,
                          a.flags, a.stream);
 }
