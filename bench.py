@@ -518,8 +518,13 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_o
         "plain_loop_msgs_per_s": round(2 * k / (plain_loop_ms / 1e3), 1),
         "plain_graph_msgs_per_s": round(2 * k / (plain_graph_ms / 1e3), 1),
         "speedup_vs_plain_graph": round((msgs / batched_ms) / (2 * k / plain_graph_ms), 1),
-        "gpu_launches_per_batched_step": 9,
+        # encode: 3 scan kernels + the flat and the per-warp kernel (one of
+        # the two returns at once); decode: the same + the finish kernel
+        "gpu_launches_per_batched_step": BATCHED_LAUNCHES,
     }
+
+
+BATCHED_LAUNCHES = 11  # kernels of one batched encode + decode step
 
 
 def batched_line(args, d: Dist):
@@ -536,7 +541,7 @@ def batched_line(args, d: Dist):
         "data": "synthetic: log-normal lengths (median 2 KiB, sigma 1.5), uniform bytes, seed 2",
         "config": {"workload": "batched encode+decode: 100,000 messages (config 3)",
                    "l2": "600 MiB of input > L2 (no flush)"},
-        "batched": b, "gpu_launches": 9 * max(args.steps, 5),
+        "batched": b, "gpu_launches": BATCHED_LAUNCHES * max(args.steps, 5),
     }
 
 
