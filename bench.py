@@ -56,6 +56,9 @@ def parse_args(argv=None):
     p.add_argument("--small", action="store_true",
                    help="384 MiB instead of 1 GiB (profiling captures; same launch shapes as "
                         "1 GiB); not a bench value")
+    p.add_argument("--tiny", action="store_true",
+                   help="with --config batched --small: 1,000,000 messages of about 40 bytes "
+                        "(the flat whole-batch kernels); a profiling case")
     return p.parse_args(argv)
 
 
@@ -410,7 +413,8 @@ def run_e2e(g, data, d: Dist):
 
 
 # ------------------------------------------------------ batched workload
-def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_override=None):
+def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_override=None,
+                lengths=None):
     """Config 3: 100,000 packed messages (seed 2). Batched: one launch per
     direction (b64_encode_batch + b64_decode_batch), direct and replayed from
     a CUDA graph. Plain: one b64_encode + one b64_decode_async per message,
@@ -425,7 +429,10 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_o
     torch.cuda.set_device(d.local_rank)
     g = pkg.load()
     dev = torch.device("cuda", d.local_rank)
-    data, off = W.batched() if nmsg_override is None else W.batched(nmsg=nmsg_override)
+    kw = {} if nmsg_override is None else {"nmsg": nmsg_override}
+    if lengths is not None:  # (median, sigma, max_len) of the log-normal lengths
+        kw.update(median=lengths[0], sigma=lengths[1], max_len=lengths[2])
+    data, off = W.batched(**kw)
     nmsg = off.size - 1
     src = torch.from_numpy(data).to(dev)
     doff = torch.from_numpy(off).to(dev)
@@ -528,6 +535,11 @@ BATCHED_LAUNCHES = 11  # kernels of one batched encode + decode step
 
 
 def batched_line(args, d: Dist):
+    if args.small and args.tiny:  # 1,000,000 short messages, batched calls only
+        b = run_batched(args, d, steps=max(args.steps, 5), plain_msgs=0, nmsg_override=1_000_000,
+                        lengths=(40.0, 0.3, 64))
+        return {"metric": "batched msgs/s (profiling case, not a bench value)",
+                "value": b["batched_msgs_per_s"], "unit": "msgs/s", "batched": b}
     if args.small:  # 20,000 messages, batched calls only (profiling captures)
         b = run_batched(args, d, steps=max(args.steps, 5), plain_msgs=0, nmsg_override=20_000)
         return {"metric": "batched msgs/s (profiling case, not a bench value)",
