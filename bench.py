@@ -705,8 +705,77 @@ def run_sweep(args, d: Dist):
     return rows
 
 
+def run_variants(args, d: Dist):
+    """The variant flags on 256 MiB of uniform random bytes (single-buffer
+    calls, CUDA-event time per call): base64url, unpadded, Appendix A's
+    strict tail, and Appendix B's whitespace removal on MIME-style input
+    (CRLF after every 76 characters) against the plain decode of the same
+    characters without the line breaks."""
+    import torch
+
+    import paper_1704_00605_gb300 as pkg
+    from paper_1704_00605_gb300 import workloads as W
+
+    torch.cuda.set_device(d.local_rank)
+    g = pkg.load()
+    dev = torch.device("cuda", d.local_rank)
+    stream = torch.cuda.current_stream(dev)
+    n = 256 << 20
+    src = W.counter_bytes_torch(8, 0, n, device=dev)
+    res = torch.empty(3, dtype=torch.int64, device=dev)
+
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e3  # microseconds per call
+
+    out = {"bytes": n}
+    dec = torch.empty(n + 16, dtype=torch.uint8, device=dev)
+
+    def result():  # (first_bad, outlen, status) of the last decode
+        return int(res[0]), int(res[1]), int(res.view(torch.int32)[4])
+
+    for name, flags in (("plain", 0), ("url", 1), ("nopad", 2), ("strict", 4)):
+        enc = g.b64_encode_ex(src, flags & 3)
+        e_us = timed(lambda: g.b64_encode_ex(src, flags & 3, enc))
+        d_us = timed(lambda: g.b64_decode_async_ex(enc, dec, res, flags))
+        assert result() == (enc.numel(), n, 0), name
+        out[name] = {"encode_us": round(e_us, 2), "decode_us": round(d_us, 2),
+                     "encode_input_gbs": round(n / e_us / 1e3, 1),
+                     "decode_input_gbs": round(enc.numel() / d_us / 1e3, 1)}
+    # MIME-style lines: 76 characters, then CR LF
+    enc = g.b64_encode(src)
+    m = enc.numel()
+    rows = (m + 75) // 76
+    body = torch.zeros(rows * 76, dtype=torch.uint8, device=dev)
+    body[:m] = enc
+    lines = torch.empty(rows, 78, dtype=torch.uint8, device=dev)
+    lines[:, :76] = body.view(rows, 76)
+    lines[:, 76] = 13
+    lines[:, 77] = 10
+    wrapped = lines.view(-1)
+    last = m - (rows - 1) * 76  # characters on the last line
+    if last != 76:
+        wrapped = torch.cat([wrapped[:(rows - 1) * 78 + last], wrapped.new_tensor([13, 10])])
+    del body, lines
+    w_us = timed(lambda: g.b64_decode_async_ex(wrapped, dec, res, 8), 10)
+    assert result() == (wrapped.numel(), n, 0)
+    assert torch.equal(dec[:n], src)
+    out["whitespace"] = {"chars": int(wrapped.numel()), "line": 76, "decode_us": round(w_us, 2),
+                         "decode_input_gbs": round(wrapped.numel() / w_us / 1e3, 1),
+                         "plain_decode_us": out["plain"]["decode_us"]}
+    return out
+
+
 def sweep_line(args, d: Dist):
     rows = run_sweep(args, d)
+    variants = run_variants(args, d)
     top = rows[-1]
     return {
         "metric": "encode/decode input GB/s against input length (Fig. 10 sweep)",
@@ -714,7 +783,7 @@ def sweep_line(args, d: Dist):
         "ms_per_step": top["encode_us"] / 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic: uniform random bytes",
         "config": {"workload": "length sweep 16 B .. 1 GiB, single calls and 256 MiB batches"},
-        "sweep": rows,
+        "sweep": rows, "variants_256mib": variants,
     }
 
 

@@ -2,12 +2,14 @@
 // return are dropped before decoding, and the first bad index is reported in
 // offsets of the original input.
 //
-//   1. k_ws_count:    per tile of kWsTile characters, the number kept.
+//   1. k_ws_count:    per tile of kWsTile characters (64 per thread), the
+//                     number kept; whitespace is found four bytes at a time.
 //   2. k_ws_scan_*:   exclusive prefix of the tile counts (three phases);
 //                     prefix[ntiles] is the compacted length m'.
 //   3. k_ws_compact:  every CTA packs its tile's kept characters at its
-//                     prefix (warp ballots/popc + a block scan of the
-//                     per-thread counts) into a scratch buffer.
+//                     prefix (a block scan of the per-thread counts) in
+//                     shared memory and writes them to a scratch buffer with
+//                     one bulk store.
 //   4. the single-buffer decode kernels, reading m' from device memory.
 //   5. k_ws_map_result: maps first_bad from compacted to original offsets
 //                     (binary search over the tile prefix, then a warp scan
@@ -22,39 +24,54 @@ namespace gb64 {
 namespace {
 
 constexpr int kWsThreads = 256;
-constexpr int64_t kWsTile = kWsThreads * 16;  // characters per tile
+constexpr int kWsPerThread = 64;                          // characters per thread
+constexpr int64_t kWsTile = kWsThreads * kWsPerThread;  // characters per tile
 constexpr int kScanThreads = 256;
 constexpr int64_t kScanChunk = kScanThreads * 4;
 
-__device__ __forceinline__ bool is_ws(uint32_t x) { return x == 0x20 || x == 0x0A || x == 0x0D; }
-
-// Keep-mask (bit k = character k is not whitespace) of 16 characters.
-__device__ __forceinline__ uint32_t keep_mask16(const uint8_t* p, int64_t avail) {
-  uint32_t mask = 0;
-  for (int k = 0; k < 16; ++k)
-    if (k < avail && !is_ws(p[k])) mask |= 1u << k;
-  return mask;
+// High bit of every byte of x that is zero (exact, no carries between bytes).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+  return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
 }
 
-// The 16 characters a thread owns, as four words, plus their keep-mask.
-__device__ __forceinline__ uint32_t load_unit(const uint8_t* src, int64_t m, int64_t at,
-                                              uint4* w) {
-  const int64_t avail = m - at;
-  if (avail >= 16) {
-    *w = load16_any(src + at, src, src + m);
-    uint32_t mask = 0;
-    const uint32_t ws[4] = {w->x, w->y, w->z, w->w};
+// Keep bits (bit k = byte k of w is not space, line feed or carriage return).
+__device__ __forceinline__ uint32_t keep4(uint32_t w) {
+  const uint32_t ws = zero_bytes(w ^ 0x20202020u) | zero_bytes(w ^ 0x0A0A0A0Au) |
+                      zero_bytes(w ^ 0x0D0D0D0Du);
+  const uint32_t keep = ~ws & 0x80808080u;
+  return ((keep >> 7) * 0x10204080u) >> 28;  // bits 7, 15, 23, 31 -> bits 0..3
+}
+
+// The 64 characters [at, at + 64) a thread owns, as 16 words (characters
+// past m read as space), and their keep-mask (bit k = character k kept).
+__device__ __forceinline__ uint64_t load_chars(const uint8_t* src, int64_t m, int64_t at,
+                                               uint32_t* w) {
+  if (m - at >= kWsPerThread) {
+    uint4 v[4];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (!is_ws((ws[k >> 2] >> (8 * (k & 3))) & 0xFFu)) mask |= 1u << k;
-    return mask;
+    for (int i = 0; i < 4; ++i) v[i] = load16_any(src + at + 16 * i, src, src + m);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[4 * i] = v[i].x;
+      w[4 * i + 1] = v[i].y;
+      w[4 * i + 2] = v[i].z;
+      w[4 * i + 3] = v[i].w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      uint32_t x = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int64_t q = at + 4 * i + k;
+        x |= (q < m ? (uint32_t)src[q] : 0x20u) << (8 * k);
+      }
+      w[i] = x;
+    }
   }
-  uint32_t b[16];
-  for (int k = 0; k < 16; ++k) b[k] = (k < avail) ? src[at + k] : 0u;
-  *w = make_uint4(b[0] | b[1] << 8 | b[2] << 16 | b[3] << 24, b[4] | b[5] << 8 | b[6] << 16 | b[7] << 24,
-                  b[8] | b[9] << 8 | b[10] << 16 | b[11] << 24,
-                  b[12] | b[13] << 8 | b[14] << 16 | b[15] << 24);
-  return avail > 0 ? keep_mask16(src + at, avail) : 0u;
+  uint64_t mask = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) mask |= (uint64_t)keep4(w[i]) << (4 * i);
+  return mask;
 }
 
 // Block-wide exclusive scan of one int per thread (kWsThreads threads).
@@ -87,9 +104,9 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
 
 __global__ void __launch_bounds__(kWsThreads)
     k_ws_count(const uint8_t* __restrict__ src, int64_t m, int64_t* __restrict__ counts) {
-  const int64_t at = blockIdx.x * kWsTile + 16 * (int64_t)threadIdx.x;
-  uint4 w;
-  const int c = __popc(load_unit(src, m, at, &w));
+  const int64_t at = blockIdx.x * kWsTile + (int64_t)kWsPerThread * threadIdx.x;
+  uint32_t w[16];
+  const int c = __popcll(load_chars(src, m, at, w));
   int total;
   block_excl_scan(c, &total);
   if (threadIdx.x == 0) counts[blockIdx.x] = total;
@@ -152,45 +169,103 @@ __global__ void k_ws_scan_add(int64_t* __restrict__ v, int64_t n, const int64_t*
   if (i == 0) v[n] = sums[nb];
 }
 
+// Packs the tile's kept characters in shared memory at the output's phase
+// (shared position o2 + i holds output byte i, o2 = the output address mod
+// 16), then writes them out: the aligned interior by one bulk store, the
+// ragged ends (at most 15 bytes each) by byte stores.
 __global__ void __launch_bounds__(kWsThreads)
     k_ws_compact(const uint8_t* __restrict__ src, int64_t m, const int64_t* __restrict__ prefix,
                  uint8_t* __restrict__ out) {
-  const int64_t at = blockIdx.x * kWsTile + 16 * (int64_t)threadIdx.x;
-  uint4 w;
-  const uint32_t mask = load_unit(src, m, at, &w);
+  __shared__ __align__(16) uint8_t buf[kWsTile + 32];
+  const int64_t at = blockIdx.x * kWsTile + (int64_t)kWsPerThread * threadIdx.x;
+  uint32_t w[16];
+  const uint64_t mask = load_chars(src, m, at, w);
   int total;
-  int64_t o = prefix[blockIdx.x] + block_excl_scan(__popc(mask), &total);
-  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+  const int local = block_excl_scan(__popcll(mask), &total);
+  uint8_t* d = out + prefix[blockIdx.x];
+  const uintptr_t da = reinterpret_cast<uintptr_t>(d);
+  const uint32_t o2 = (uint32_t)(da & 15u);
+  uint32_t p = o2 + (uint32_t)local;
 #pragma unroll
-  for (int k = 0; k < 16; ++k)
-    if (mask & (1u << k)) out[o++] = (uint8_t)(ws[k >> 2] >> (8 * (k & 3)));
+  for (int i = 0; i < 16; ++i) {
+    const uint32_t k4 = (uint32_t)(mask >> (4 * i)) & 15u;
+    if (k4 == 15u) {  // the common case: four characters kept
+      buf[p] = (uint8_t)w[i];
+      buf[p + 1] = (uint8_t)(w[i] >> 8);
+      buf[p + 2] = (uint8_t)(w[i] >> 16);
+      buf[p + 3] = (uint8_t)(w[i] >> 24);
+      p += 4;
+    } else {
+      for (int k = 0; k < 4; ++k)
+        if (k4 & (1u << k)) buf[p++] = (uint8_t)(w[i] >> (8 * k));
+    }
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  const uint32_t olen = (uint32_t)total;
+  const uintptr_t lo = (da + 15u) & ~(uintptr_t)15u, hi = (da + olen) & ~(uintptr_t)15u;
+  if (threadIdx.x == 0 && hi > lo) {
+    tma_store_1d(reinterpret_cast<void*>(lo), buf + (o2 ? 16u : 0u), (uint32_t)(hi - lo));
+    bulk_commit();
+  }
+  const uint32_t head = (uint32_t)(tmin<uintptr_t>(lo, da + olen) - da);
+  const uint32_t ie = hi > lo ? (uint32_t)(hi - da) : head;
+  const uint32_t t = threadIdx.x;
+  if (t < head) {
+    d[t] = buf[o2 + t];
+  } else if (t >= 32u && t - 32u < olen - ie) {
+    d[ie + t - 32u] = buf[o2 + ie + t - 32u];
+  }
+  if (threadIdx.x == 0) bulk_wait_all();  // the CTA's shared memory outlives the copy
 }
 
-// Original index of compacted character k (k < prefix[ntiles]).
+__device__ __forceinline__ bool is_ws(uint32_t x) { return x == 0x20 || x == 0x0A || x == 0x0D; }
+
+// Original index of compacted character k (k < prefix[ntiles]), by one
+// warp: the tile holding it (binary search of the tile prefix), then the
+// kept characters of each lane's 1/32 of the tile counted and prefixed, then
+// one lane's scan of its part.
 __device__ int64_t original_index(const uint8_t* src, int64_t m, const int64_t* prefix,
-                                  int64_t ntiles, int64_t k) {
+                                  int64_t ntiles, int64_t k, uint32_t lane) {
   int64_t lo = 0, hi = ntiles;  // prefix[lo] <= k < prefix[hi]
   while (hi - lo > 1) {
     const int64_t mid = (lo + hi) / 2;
     if (prefix[mid] <= k) lo = mid; else hi = mid;
   }
-  int64_t left = k - prefix[lo];
-  const int64_t end = tmin<int64_t>(m, (lo + 1) * kWsTile);
-  for (int64_t i = lo * kWsTile; i < end; ++i)
-    if (!is_ws(src[i]) && left-- == 0) return i;
-  return m;  // not reached for a valid k
+  const int64_t part = kWsTile / 32;
+  const int64_t b = lo * kWsTile + lane * part, e = tmin<int64_t>(m, b + part);
+  int c = 0;
+  for (int64_t i = b; i < e; ++i) c += !is_ws(src[i]);
+  int incl = c;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if ((int)lane >= d) incl += y;
+  }
+  const int64_t left = k - prefix[lo];  // kept characters of the tile before k
+  const bool mine = left >= incl - c && left < incl;
+  int64_t r = m;
+  if (mine) {
+    int64_t n = left - (incl - c);
+    for (int64_t i = b; i < e; ++i)
+      if (!is_ws(src[i]) && n-- == 0) {
+        r = i;
+        break;
+      }
+  }
+  const uint32_t who = __ballot_sync(0xFFFFFFFFu, mine);
+  return who ? __shfl_sync(0xFFFFFFFFu, r, __ffs(who) - 1) : m;
 }
 
 __global__ void k_ws_map_result(b64_result* res, const uint8_t* __restrict__ src, int64_t m,
                                 const int64_t* __restrict__ prefix, int64_t ntiles) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (res->status == B64_OK) {
-    res->first_bad = m;
-  } else if (res->status > 0 && res->first_bad < prefix[ntiles]) {
-    res->first_bad = original_index(src, m, prefix, ntiles, res->first_bad);
-  } else if (res->status > 0) {
-    res->first_bad = m;
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const uint32_t lane = threadIdx.x;
+  const int32_t status = res->status;
+  const int64_t fb = res->first_bad;
+  int64_t out = m;
+  if (status > 0 && fb < prefix[ntiles]) out = original_index(src, m, prefix, ntiles, fb, lane);
+  __syncwarp();
+  if (lane == 0 && status >= 0) res->first_bad = out;
 }
 
 }  // namespace

@@ -152,6 +152,66 @@ def test_workload_error_batch_reduced(gb64, oracle):
     assert (est != 0).sum() == rec["err_msg"].size
 
 
+def test_workload_error_batch_full(gb64, oracle):
+    """Config 4 at full size: 1,000,000 messages of 16 B .. 64 KiB (about
+    33 GB of payload, generated on the device from the counter-based
+    stream), encoded and decoded in one launch per direction in the default
+    shapes. Every message: status, first_bad and outlen exact (the 10,000
+    injected errors at their known offsets, every other message OK with its
+    length); sampled messages (with and without an error) against the oracle
+    one by one; the round trip of every clean message is checked on the
+    device."""
+    import torch
+
+    rec = W.error_batch(seed=3)
+    off = rec["in_off"]
+    nmsg = off.size - 1
+    doff = dev(off)
+    payload = W.counter_bytes_torch(rec["payload_key"], 0, int(off[-1]), device="cuda")
+    enc, eoff = gb64.b64_encode_batch(payload, doff)
+    eo = eoff.cpu().numpy()
+    rng = np.random.default_rng(5)
+    sample = np.concatenate([rng.integers(0, nmsg, 120), rec["err_msg"][:40]])
+    for j in sample:  # encodings against the oracle before any error is written
+        raw = W.counter_bytes(rec["payload_key"], int(off[j]), int(off[j + 1] - off[j]))
+        assert np.array_equal(enc[eo[j]:eo[j + 1]].cpu().numpy(), oracle.encode(raw)), j
+    pos = W.inject_errors(enc, eo, rec["err_msg"], rec["err_frac"], rec["err_byte"])
+    dst, out_off, st, fb, ol = gb64.b64_decode_batch(enc, eoff)
+    st, fb, ol = st.cpu().numpy(), fb.cpu().numpy(), ol.cpu().numpy()
+    bad = np.zeros(nmsg, dtype=bool)
+    bad[rec["err_msg"]] = True
+    assert (st[~bad] == 0).all() and (ol[~bad] == np.diff(off)[~bad]).all()
+    assert (fb[~bad] == np.diff(eo)[~bad]).all()
+    assert (st[bad] == 1).all()  # an injected byte is never in the alphabet nor '='
+    assert np.array_equal(fb[rec["err_msg"]], pos - eo[rec["err_msg"]])
+    oo = out_off.cpu().numpy()
+    for j in sample:  # decode results against the oracle
+        m = enc[eo[j]:eo[j + 1]].cpu().numpy()
+        est, eout, efb = oracle.decode(m)
+        assert (st[j], fb[j]) == (est, efb), j
+        if est == 0:
+            assert np.array_equal(dst[oo[j]:oo[j] + ol[j]].cpu().numpy(), eout), j
+    # every clean message decodes to its payload: gather the decoded bytes of
+    # 20,000 messages at a time (at most ~1.3 GB of payload, 10 GB of int64
+    # indices) and blank the messages with an error on both sides
+    lens = torch.diff(doff)
+    badd = torch.from_numpy(bad).cuda()
+    step = 20_000
+    for a in range(0, nmsg, step):
+        b = min(nmsg, a + step)
+        ln = lens[a:b]
+        n = int(off[b] - off[a])
+        idx = torch.repeat_interleave(out_off[a:b], ln) + (
+            torch.arange(n, device="cuda") - torch.repeat_interleave(doff[a:b] - doff[a], ln))
+        got = dst[idx]
+        want = payload[int(off[a]):int(off[b])].clone()
+        mask = torch.repeat_interleave(badd[a:b], ln)
+        got[mask] = 0
+        want[mask] = 0
+        assert torch.equal(got, want), a
+        del idx, got, want, mask
+
+
 def test_batch_deterministic_and_stream_ordered(gb64, oracle):
     import torch
 
