@@ -316,6 +316,30 @@ __device__ __forceinline__ uint32_t byte_of(uint4 c, uint32_t k) {
   return (word_of(c, k >> 2) >> (8u * (k & 3u))) & 0xFFu;
 }
 
+// cnt whole chunks: chunk i encodes the 12 stage bytes at sb + 12i (sb + 12i
+// is R mod 4 for every i) and goes to the aligned 16 bytes at db + 16i.
+template <int R>
+__device__ __forceinline__ void enc_chunks(const uint8_t* sb, uint8_t* db, int32_t cnt,
+                                           uint32_t lane, const uint8_t* T) {
+  const uint32_t* wb = reinterpret_cast<const uint32_t*>(sb - R);
+#pragma unroll 2
+  for (int32_t i = (int32_t)lane; i < cnt; i += 32) {
+    const uint32_t* q = wb + 3 * i;
+    uint32_t x, y, z;
+    if (R == 0) {
+      x = q[0];
+      y = q[1];
+      z = q[2];
+    } else {
+      const uint32_t q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+      x = __funnelshift_r(q0, q1, 8 * R);
+      y = __funnelshift_r(q1, q2, 8 * R);
+      z = __funnelshift_r(q2, q3, 8 * R);
+    }
+    st_global_v4_cs(db + 16 * i, enc_unit(x, y, z, T));
+  }
+}
+
 // Encodes one tile (Algorithm 1 per 12-byte unit) straight to global memory
 // in aligned 16-byte stores; the message's last tile also codes the partial
 // group with its padding.
@@ -337,19 +361,48 @@ __device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in
   uint8_t* abase = dp - o2;  // 16-byte aligned
   if ((o2 & 3u) == 0) {
     const uint32_t q = o2 >> 2;
-    const uint32_t nc = nu == 0 ? 0u : (q ? nu + 1u : nu);
-#pragma unroll 2
-    for (uint32_t c = lane; c < nc; c += 32u) {
-      const bool head = q && c == 0, tail = q && c == nu;
-      const uint32_t off = head ? 0u : (tail ? 12u * (nu - 1u) : 12u * c - 3u * q);
+    // whole chunks c in [cf, nu): input offset 12c - 3q, stage position
+    // p0 + 12c; those whose 12 bytes were all copied, [c_lo, c_hi), take
+    // the loop specialised on the stage's 4-byte phase
+    const int32_t cf = q ? 1 : 0, n = (int32_t)nu;
+    const int32_t p0 = (int32_t)v.o - 3 * (int32_t)q;
+    const int32_t c_lo = n > 0 ? min(n, max(cf, ((int32_t)v.ia - p0 + 11) / 12)) : 0;
+    const int32_t room = (int32_t)v.ib - 12 - p0;  // last copied chunk start
+    const int32_t c_hi = room < 0 ? c_lo : max(c_lo, min(n, room / 12 + 1));
+    if (c_hi > c_lo) {
+      const uint8_t* sb = in + (p0 + 12 * c_lo);
+      uint8_t* db = abase + 16u * (uint32_t)c_lo;
+      const int32_t cnt = c_hi - c_lo;
+      switch ((p0 + 12 * c_lo) & 3) {
+        case 0: enc_chunks<0>(sb, db, cnt, lane, T); break;
+        case 1: enc_chunks<1>(sb, db, cnt, lane, T); break;
+        case 2: enc_chunks<2>(sb, db, cnt, lane, T); break;
+        default: enc_chunks<3>(sb, db, cnt, lane, T); break;
+      }
+    }
+    // the rest: chunks outside the copied part, and with q > 0 the partial
+    // chunks at both ends (chunk 0 keeps the first 4 - q words of unit 0's
+    // characters, chunk nu the last q words of unit nu - 1's)
+    const int32_t nedge = n == 0 ? 0 : (c_lo - cf) + (n - c_hi) + (q ? 2 : 0);
+    for (int32_t k = (int32_t)lane; k < nedge; k += 32) {
+      int32_t c;
+      if (k < c_lo - cf) {
+        c = cf + k;
+      } else if (k < (c_lo - cf) + (n - c_hi)) {
+        c = c_hi + (k - (c_lo - cf));
+      } else {
+        c = (k == nedge - 2) ? 0 : n;  // the two partial chunks
+      }
+      const bool head = q && c == 0, tail = q && c == n;
+      const uint32_t off = head ? 0u : (tail ? 12u * (nu - 1u) : 12u * (uint32_t)c - 3u * q);
       const uint3 w = enc_load(v, in, sp, off);
       const uint4 e = enc_unit(w.x, w.y, w.z, T);
       if (!head && !tail) {
-        st_global_v4_cs(abase + 16u * c, e);
+        st_global_v4_cs(abase + 16u * (uint32_t)c, e);
       } else {
         uint32_t* wd = reinterpret_cast<uint32_t*>(head ? dp : dp + 16u * nu - 4u * q);
         const uint32_t k0 = head ? 0u : 4u - q, nk = head ? 4u - q : q;
-        for (uint32_t k = 0; k < nk; ++k) wd[k] = word_of(e, k0 + k);
+        for (uint32_t i = 0; i < nk; ++i) wd[i] = word_of(e, k0 + i);
       }
     }
   } else {
@@ -448,26 +501,14 @@ __device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in
   const uint32_t o2 = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15u);
   unsigned long long bad = ~0ull;
   uint32_t carry = 0;  // last word of the previous row's last unit
-  // Two rows per pass, as in encode_tile.
-  for (uint32_t base = 0; base < nu; base += 64u) {
-    const uint32_t ua = base + lane, ub = ua + 32u;
-    const bool two = base + 32u < nu;
-    uint4 wa = make_uint4(0u, 0u, 0u, 0u), wb = wa;
-    if (ua < nu) wa = dec_load(v, in, ua);
-    if (two && ub < nu) wb = dec_load(v, in, ub);
-    uint32_t ea = 0, eb = 0;
-    const uint3 oa = dec_unit(wa, D, ea);
-    uint3 ob = make_uint3(0u, 0u, 0u);
-    if (two) ob = dec_unit(wb, D, eb);
-    if (((ea | eb) & kBadFlag) && bad == ~0ull) {
-      if ((ea & kBadFlag) && ua < nu) {
-        bad = t0 + 16u * ua + dec_unit_first_bad(wa, D);
-      } else if ((eb & kBadFlag) && ub < nu) {
-        bad = t0 + 16u * ub + dec_unit_first_bad(wb, D);
-      }
-    }
-    dec_store_row(out, o2, ua, nu, oa, carry, lane);
-    if (two) dec_store_row(out, o2, ub, nu, ob, carry, lane);
+  for (uint32_t base = 0; base < nu; base += 32u) {
+    const uint32_t u = base + lane;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (u < nu) w = dec_load(v, in, u);
+    uint32_t err = 0;
+    const uint3 o = dec_unit(w, D, err);
+    if ((err & kBadFlag) && u < nu && bad == ~0ull) bad = t0 + 16u * u + dec_unit_first_bad(w, D);
+    dec_store_row(out, o2, u, nu, o, carry, lane);
   }
   warp_min_to(fb, bad);
   const uint32_t nq = (body - 16u * nu) / 4u;
