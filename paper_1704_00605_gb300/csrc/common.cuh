@@ -341,20 +341,6 @@ __device__ __forceinline__ void store16_any(uint8_t* p, uint4 v) {
   }
 }
 
-__device__ __forceinline__ void store12_any(uint8_t* p, uint3 v) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  if ((a & 3u) == 0) {
-    uint32_t* q = reinterpret_cast<uint32_t*>(p);
-    q[0] = v.x;
-    q[1] = v.y;
-    q[2] = v.z;
-  } else {
-    const uint32_t w[3] = {v.x, v.y, v.z};
-#pragma unroll
-    for (int k = 0; k < 12; ++k) p[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
-  }
-}
-
 __device__ __forceinline__ void store4_any(uint8_t* p, uint32_t w) {
   if ((reinterpret_cast<uintptr_t>(p) & 3u) == 0) {
     *reinterpret_cast<uint32_t*>(p) = w;

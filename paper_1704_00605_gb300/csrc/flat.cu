@@ -119,8 +119,8 @@ __device__ __forceinline__ void flat_issue(const FlatTile& v, const uint8_t* src
   }
 }
 
-// Stage-or-global byte / 12-byte reads of the input at absolute offset X
-// (the stage holds offsets from x0 on).
+// Stage-or-global byte reads of the input at absolute offset X (the stage
+// holds offsets from x0 on).
 struct StageReader {
   const uint8_t* stage;
   const uint8_t* src;
@@ -132,9 +132,6 @@ struct StageReader {
   }
   __device__ __forceinline__ uint32_t byte(int64_t X) const {
     return inside(X, 1) ? (uint32_t)stage[o + (uint32_t)(X - x0)] : (uint32_t)src[X];
-  }
-  __device__ __forceinline__ uint3 word12(int64_t X) const {
-    return inside(X, 12) ? lds12(stage + o + (uint32_t)(X - x0)) : load12_any(src + X, src, src + total);
   }
 };
 
