@@ -241,14 +241,35 @@ struct TileView {
   uint32_t ia, ib;
 };
 
-// The view of tile t, advancing the message cursor j (tile_off is
-// non-decreasing and t < tile_off[nmsg]).
+// The issuing lane's walk over its tiles: the current message is kept in
+// the warp's slot of shared memory (not in registers, which every lane would
+// pay for), so the offsets arrays are read only when the walk enters the
+// next message (tile_off is non-decreasing; tiles are visited in order).
+struct WalkState {
+  Msg m;
+  int64_t j;        // current message
+  int64_t t_first;  // its first tile
+  int64_t t_end;    // one past its last tile
+};
+
 template <class Msgs>
-__device__ __forceinline__ TileView tile_view(const Msgs& ms, const int64_t* tile_off, int64_t t,
-                                              int64_t& j, int64_t tile, int64_t out_tile) {
-  while (__ldg(tile_off + j + 1) <= t) ++j;
-  const Msg m = ms.get(j);
-  const int64_t k = t - __ldg(tile_off + j);
+__device__ __forceinline__ void walk_load(WalkState& w, const Msgs& ms, const int64_t* tile_off) {
+  w.m = ms.get(w.j);
+  w.t_first = __ldg(tile_off + w.j);
+  w.t_end = __ldg(tile_off + w.j + 1);
+}
+
+// The view of tile t (t >= the previous tile asked for).
+template <class Msgs>
+__device__ __forceinline__ TileView walk_view(WalkState& w, const Msgs& ms,
+                                              const int64_t* tile_off, int64_t t, int64_t tile,
+                                              int64_t out_tile) {
+  while (t >= w.t_end) {
+    ++w.j;
+    walk_load(w, ms, tile_off);
+  }
+  const Msg m = w.m;
+  const int64_t k = t - w.t_first;
   TileView v;
   v.msrc = m.src;
   v.mout = m.out;
@@ -257,7 +278,7 @@ __device__ __forceinline__ TileView tile_view(const Msgs& ms, const int64_t* til
   v.dst = m.out + k * out_tile;
   v.t0 = k * tile;
   v.mlen = m.len;
-  v.j = j;
+  v.j = w.j;
   v.len = (uint32_t)tmin<int64_t>(tile, m.len - v.t0);
   const uintptr_t s = reinterpret_cast<uintptr_t>(m.src + v.t0);
   const uintptr_t a = (s + 15u) & ~(uintptr_t)15u, b = (s + v.len) & ~(uintptr_t)15u;
@@ -567,6 +588,7 @@ __global__ void __launch_bounds__(NT)
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
   __shared__ TileView meta[NT / 32][kMaxBatchStages];
+  __shared__ WalkState walks[NT / 32];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t S = stages;
   if (lane == 0) {
@@ -591,10 +613,12 @@ __global__ void __launch_bounds__(NT)
   if (t_begin >= t_end) return;
   Msgs ms = msgs;
   ms.prepare(nmsg);
+  WalkState& walk = walks[warp];  // used by lane 0
   if (lane == 0) {
-    int64_t ji = owner_of(tile_off, nmsg, t_begin);
+    walk.j = owner_of(tile_off, nmsg, t_begin);
+    walk_load(walk, ms, tile_off);
     for (uint32_t s = 0; s < S && t_begin + s < t_end; ++s) {
-      meta[warp][s] = tile_view(ms, tile_off, t_begin + s, ji, tile, out_tile);
+      meta[warp][s] = walk_view(walk, ms, tile_off, t_begin + s, tile, out_tile);
       issue_tile(meta[warp][s], wbase + s * in_b, &full[warp][s]);
     }
   }
@@ -622,8 +646,7 @@ __global__ void __launch_bounds__(NT)
       __syncwarp();
     }
     if (lane == 0 && t + S < t_end) {
-      int64_t ji = v.j;
-      meta[warp][s] = tile_view(ms, tile_off, t + S, ji, tile, out_tile);
+      meta[warp][s] = walk_view(walk, ms, tile_off, t + S, tile, out_tile);
       issue_tile(meta[warp][s], in, &full[warp][s]);
     }
     if (++s == S) {

@@ -111,16 +111,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// As mbar_wait_bounded, but sleeping briefly between polls, so that warps
-// waiting for their next tile leave the issue slots to the warps computing.
+// try_wait with a suspend-time hint: the thread may sleep until the phase
+// completes or about `ns` nanoseconds pass, instead of polling.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// As mbar_wait_bounded, but letting the hardware suspend the waiting warp
+// until the phase completes, so that warps waiting for their next tile
+// leave the issue slots to the warps computing.
 __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  for (uint32_t i = 0;; ++i) {
-    __nanosleep(64);
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15u) == 15u && global_timer_ns() - t0 > limit_ns) return false;
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity, 100000u)) return true;
+    if (global_timer_ns() - t0 > limit_ns) return false;
   }
 }
 
