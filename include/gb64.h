@@ -152,8 +152,8 @@ enum {
  * multiple of 384 up to 6144, or characters, a multiple of 512 up to
  * 8192), stages (input stages per warp, 2..6; 0 = 4) and blocks_per_sm
  * (0 = as many as fit) of the per-warp tile kernels; the shape's shared
- * memory, threads / 32 * (stages * (tile + 32) + (decode only) 2 *
- * (3 * tile / 4 + 32)) bytes, must stay within 219 KiB. For batch kinds
+ * memory, threads / 32 * (stages * (tile + 32) + (decode only)
+ * 3 * tile / 4 + 32) bytes, must stay within 219 KiB. For batch kinds
  * units_per_thread selects the kernel of packed batches whose input
  * (decode) or output (padded encode) starts on a 16-byte boundary: 0 = the
  * flat whole-batch kernels when the mean message length is short (decided

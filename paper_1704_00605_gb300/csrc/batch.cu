@@ -570,7 +570,7 @@ __host__ __device__ __forceinline__ int64_t out_tile_bytes(int decode, int64_t t
 }
 __host__ __device__ __forceinline__ uint32_t warp_smem_bytes(int decode, int64_t tile,
                                                              uint32_t stages) {
-  return stages * stage_in_bytes(tile) + (decode ? 2u * ((uint32_t)out_tile_bytes(1, tile) + 32u) : 0u);
+  return stages * stage_in_bytes(tile) + (decode ? (uint32_t)out_tile_bytes(1, tile) + 32u : 0u);
 }
 
 // The persistent kernel of both directions: warp w of the grid's G warps
@@ -601,9 +601,9 @@ __global__ void __launch_bounds__(NT)
     init_tables(table, nullptr, flags & kFlagUrl);
   }
   const int64_t out_tile = out_tile_bytes(DECODE, tile);
-  const uint32_t in_b = stage_in_bytes(tile), out_b = (uint32_t)out_tile + 32u;
+  const uint32_t in_b = stage_in_bytes(tile);
   uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, tile, S);
-  uint8_t* obase = wbase + S * in_b;  // decode: the two output buffers
+  uint8_t* obase = wbase + S * in_b;  // decode: the output buffer
 
   const int64_t total = __ldg(tile_off + nmsg);
   const int64_t nw = (int64_t)gridDim.x * (NT / 32);
@@ -635,10 +635,10 @@ __global__ void __launch_bounds__(NT)
     }
     const TileView v = meta[warp][s];
     if (DECODE) {
-      // the bulk store that last read this output buffer is done with it
-      if (lane == 0 && t - t_begin >= 2) bulk_wait_read(1);
+      // the previous tile's bulk store has finished reading the output buffer
+      if (lane == 0 && t > t_begin) bulk_wait_read(0);
       __syncwarp();
-      decode_tile(v, in, obase + ((uint32_t)(t - t_begin) & 1u) * out_b, table,
+      decode_tile(v, in, obase, table,
                   reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j, lane, flags);
     } else {
       encode_tile(v, in, table, lane, flags);

@@ -77,7 +77,7 @@ cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);
 constexpr size_t kBatchSmemLimit = 227 * 1024 - 8 * 1024;
 
 // Dynamic shared memory of a batched launch: per warp, `stages` input
-// stages of a tile (and, decoding, two output buffers).
+// stages of a tile (and, decoding, one output buffer).
 size_t batch_smem_bytes(int decode, const BatchConfig& c);
 
 // Shape of the flat kernels (flat.cu), which code a packed batch as one

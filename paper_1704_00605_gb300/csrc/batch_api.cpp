@@ -23,8 +23,8 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
 // 6.3 KiB on average, and 256 of 1 MiB). mean_len < 0: unknown.
 BatchConfig default_batch_config(int decode, int64_t mean_len) {
   const bool small = mean_len >= 0 && mean_len < 1024;
-  if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 2048, 0, 2};
-  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 3072, 0, 2};
+  if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 4096, 0, 2};
+  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2};
 }
 
 namespace {

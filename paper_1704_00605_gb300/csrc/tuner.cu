@@ -145,7 +145,7 @@ std::vector<b64_shape> batch_candidates(int decode) {
   std::vector<b64_shape> out;
   const int64_t row = decode ? 512 : 384;
   for (int threads : {128, 256})
-    for (int rows : {2, 4, 8})
+    for (int rows : {2, 4, 8, 12, 16})
       for (int stages : {2, 3, 4, 6}) {
         const b64_shape s{threads, 0, stages, 0, row * rows, 0.f};
         if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
