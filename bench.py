@@ -58,7 +58,7 @@ def parse_args(argv=None):
                         "1 GiB); not a bench value")
     p.add_argument("--tiny", action="store_true",
                    help="with --config batched --small: 1,000,000 messages of about 40 bytes "
-                        "(the flat whole-batch kernels); a profiling case")
+                        "(one thread each); a profiling case")
     return p.parse_args(argv)
 
 
@@ -525,8 +525,8 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_o
         "plain_loop_msgs_per_s": round(2 * k / (plain_loop_ms / 1e3), 1),
         "plain_graph_msgs_per_s": round(2 * k / (plain_graph_ms / 1e3), 1),
         "speedup_vs_plain_graph": round((msgs / batched_ms) / (2 * k / plain_graph_ms), 1),
-        # encode: 3 scan kernels + the flat and the per-warp kernel (one of
-        # the two returns at once); decode: the same + the finish kernel
+        # encode: 3 scan kernels + the short-message and the per-warp tile
+        # kernel; decode: the same + the finish kernel
         "gpu_launches_per_batched_step": BATCHED_LAUNCHES,
     }
 

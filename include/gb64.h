@@ -154,12 +154,10 @@ enum {
  * (0 = as many as fit) of the per-warp tile kernels; the shape's shared
  * memory, threads / 32 * (stages * (tile + 32) + (decode only)
  * 3 * tile / 4 + 32) bytes, must stay within 219 KiB. For batch kinds
- * units_per_thread selects the kernel of packed batches whose input
- * (decode) or output (padded encode) starts on a 16-byte boundary: 0 = the
- * flat whole-batch kernels when the mean message length is short (decided
- * on the device), 1 = always the flat kernels, 2 = always the per-warp
- * tile kernels; other batches always take the per-warp kernels. ms is a
- * measured time. */
+ * units_per_thread selects the kernels of packed batches: 0 = messages of
+ * up to 256 bytes (encode) or 344 characters (decode) one thread each and
+ * the per-warp tile kernels for the longer ones, 1 = the per-warp tile
+ * kernels for every message. ms is a measured time. */
 typedef struct {
   int32_t threads;
   int32_t units_per_thread;

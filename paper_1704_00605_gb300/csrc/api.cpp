@@ -95,14 +95,12 @@ const DeviceInfo* device_info(cudaError_t* err) {
 }
 
 int read_and_clear_faults() {
-  unsigned a = 0, b = 0, c = 0;
+  unsigned a = 0, b = 0;
   int rc = single_read_and_clear_fault(&a);
   if (rc) return rc;
   rc = batch_read_and_clear_fault(&b);
   if (rc) return rc;
-  rc = flat_read_and_clear_fault(&c);
-  if (rc) return rc;
-  return (a | b | c) ? B64_ERR_TIMEOUT : B64_OK;
+  return (a | b) ? B64_ERR_TIMEOUT : B64_OK;
 }
 
 constexpr int kAllFlags = B64_FLAG_URL | B64_FLAG_NOPAD | B64_FLAG_STRICT_TAIL;

@@ -34,12 +34,14 @@ constexpr int64_t kScanPerBlock = (int64_t)kScanThreads * kScanItems;
 constexpr int64_t kNoBad = INT64_MAX;
 
 // ----------------------------------------------------------------- scan
+// Output length and tile count of one message; messages of at most
+// small_max bytes get no tiles (the short-message kernel codes them).
 __device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, uint32_t flags,
-                                           int64_t& outv, int64_t& tiles) {
+                                           int64_t small_max, int64_t& outv, int64_t& tiles) {
   if (len < 0) len = 0;
   outv = decode ? (int64_t)decoded_cap_flags((uint64_t)len, flags)
                 : (int64_t)encoded_len_flags((uint64_t)len, flags);
-  tiles = (len + tile - 1) / tile;
+  tiles = len > small_max ? (len + tile - 1) / tile : 0;
 }
 
 // Block-wide exclusive scan of a pair of int64 values; returns the block total.
@@ -89,8 +91,9 @@ __device__ __forceinline__ void block_exclusive_scan2(int64_t& a, int64_t& b, in
 
 __global__ void __launch_bounds__(kScanThreads)
     k_scan_local(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
-                 uint32_t flags, int64_t* __restrict__ out_off, int64_t* __restrict__ tile_off,
-                 int64_t* __restrict__ part_out, int64_t* __restrict__ part_tiles) {
+                 uint32_t flags, int64_t small_max, int64_t* __restrict__ out_off,
+                 int64_t* __restrict__ tile_off, int64_t* __restrict__ part_out,
+                 int64_t* __restrict__ part_tiles) {
   const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
   int64_t vo[kScanItems], vt[kScanItems];
   int64_t so = 0, st = 0;
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(kScanThreads)
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t j = base + i;
     vo[i] = vt[i] = 0;
-    if (j < nmsg) msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, vo[i], vt[i]);
+    if (j < nmsg)
+      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, vo[i], vt[i]);
     so += vo[i];
     st += vt[i];
   }
@@ -197,10 +201,6 @@ struct PackedMsgs {
     return __ldg(in_off + j + 1) - __ldg(in_off + j);
   }
   __device__ __forceinline__ void prepare(int64_t nmsg) { src_hi = src + __ldg(in_off + nmsg); }
-  // mean message length (the batch's bytes over its messages)
-  __device__ __forceinline__ int64_t mean_len(int64_t nmsg) const {
-    return nmsg > 0 ? __ldg(in_off + nmsg) / nmsg : 0;
-  }
 };
 
 // Messages anywhere in device memory, one descriptor each (the server).
@@ -213,7 +213,6 @@ struct DescMsgs {
   }
   __device__ __forceinline__ int64_t len(int64_t j) const { return desc[j].len; }
   __device__ __forceinline__ void prepare(int64_t) {}
-  __device__ __forceinline__ int64_t mean_len(int64_t) const { return INT64_MAX; }
 };
 
 // ------------------------------------------------------ warp pipeline
@@ -560,6 +559,144 @@ __device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in
   copy_out(dp, 12u * nu, out, lane);
 }
 
+// ------------------------------------------------------ short messages
+// One thread codes a whole message of at most small_max bytes (encode) or
+// characters (decode), straight between global memory and registers: a
+// message of a few dozen bytes then costs its own groups only, not a tile.
+__device__ __forceinline__ void encode_message(const uint8_t* p, int64_t n, uint8_t* d,
+                                               const uint8_t* T, uint32_t flags,
+                                               const uint8_t* lo, const uint8_t* hi) {
+  const uint32_t nu = (uint32_t)(n / 12);
+  for (uint32_t u0 = 0; u0 < nu; u0 += 4) {  // Algorithm 1 on 12-byte units, 4 loads ahead
+    uint3 w[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (u0 + k < nu) w[k] = load12_any(p + 12 * (u0 + k), lo, hi);
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (u0 + k < nu) store16_any(d + 16 * (u0 + k), enc_unit(w[k].x, w[k].y, w[k].z, T));
+  }
+  const uint32_t rest = (uint32_t)n - 12 * nu;
+  for (uint32_t g = 0; 3 * g < rest; ++g) {  // whole groups, then the partial one
+    const uint8_t* q = p + 12 * nu + 3 * g;
+    const uint32_t cnt = min(3u, rest - 3 * g);
+    const uint32_t b0 = q[0], b1 = cnt > 1 ? q[1] : 0u, b2 = cnt > 2 ? q[2] : 0u;
+    store_tail_group(d + 16 * nu + 4 * g, enc_tail_group(b0, b1, b2, cnt, T), cnt, flags);
+  }
+}
+
+// Sequential byte output through aligned 32-bit stores: bytes are gathered
+// in `word` until its aligned word is full; the first and last words of the
+// output, shared with the neighbouring messages, are written byte by byte.
+struct WordWriter {
+  uint8_t* start;   // first output byte
+  uint32_t* w;      // aligned word being filled
+  uint32_t word = 0;
+  uint32_t fill;    // bytes of *w before the next byte
+  __device__ __forceinline__ explicit WordWriter(uint8_t* d)
+      : start(d),
+        w(reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(d) & ~(uintptr_t)3)),
+        fill((uint32_t)(reinterpret_cast<uintptr_t>(d) & 3u)) {}
+  // appends the 4 bytes of x (little-endian)
+  __device__ __forceinline__ void put4(uint32_t x) {
+    if (fill == 0) {
+      store_full(x);
+      return;
+    }
+    const uint32_t sh = 8u * fill;
+    store_full(word | (x << sh));
+    word = x >> (32u - sh);
+  }
+  __device__ __forceinline__ void store_full(uint32_t v) {
+    if (reinterpret_cast<uint8_t*>(w) < start) {  // the first word: our bytes only
+      const uint32_t skip = (uint32_t)(start - reinterpret_cast<uint8_t*>(w));
+      for (uint32_t k = skip; k < 4; ++k) reinterpret_cast<uint8_t*>(w)[k] = (uint8_t)(v >> (8 * k));
+    } else {
+      *w = v;
+    }
+    ++w;
+  }
+  // writes the bytes still held (fewer than 4)
+  __device__ __forceinline__ void flush() {
+    for (uint32_t k = 0; k < fill; ++k) {
+      uint8_t* q = reinterpret_cast<uint8_t*>(w) + k;
+      if (q >= start) *q = (uint8_t)(word >> (8 * k));
+    }
+  }
+};
+
+// Algorithm 2 over the body (stopping at the first invalid character, whose
+// index goes to *fb), then the final characters; *outlen_j receives the
+// final group's result as for the tile kernels.
+__device__ __forceinline__ void decode_message(const uint8_t* p, int64_t m, uint8_t* d,
+                                               const uint8_t* D, unsigned long long* fb,
+                                               int64_t* outlen_j, uint32_t flags,
+                                               const uint8_t* lo, const uint8_t* hi) {
+  const uint64_t body_end = decode_body_end((uint64_t)m);
+  const uint32_t nq = (uint32_t)(body_end / 4), nu = nq / 4;
+  WordWriter out(d);
+  for (uint32_t u0 = 0; u0 < nu; u0 += 4) {  // 16-character units, 4 loads ahead
+    uint4 w[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (u0 + k < nu) w[k] = load16_any(p + 16 * (u0 + k), lo, hi);
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+      if (u0 + k >= nu) break;
+      uint32_t err = 0;
+      const uint3 o = dec_unit(w[k], D, err);
+      if (err & kBadFlag) {
+        *fb = 16ull * (u0 + k) + dec_unit_first_bad(w[k], D);
+        return;
+      }
+      out.put4(o.x);
+      out.put4(o.y);
+      out.put4(o.z);
+    }
+  }
+  out.flush();
+  for (uint32_t k = 4 * nu; k < nq; ++k) {  // the last whole quads
+    const uint8_t* c = p + 4 * k;
+    const uint32_t x = (uint32_t)c[0] | ((uint32_t)c[1] << 8) | ((uint32_t)c[2] << 16) |
+                       ((uint32_t)c[3] << 24);
+    uint32_t err = 0;
+    const uint32_t val = dec_quad(x, D, err);
+    if (err & kBadFlag) {
+      for (uint32_t i = 0; i < 4; ++i)
+        if (D[(x >> (8 * i)) & 0xFFu] & kBadFlag) {
+          *fb = 4ull * k + i;
+          return;
+        }
+    }
+    uint8_t* q = d + 3 * k;
+    q[0] = (uint8_t)(val >> 16);
+    q[1] = (uint8_t)(val >> 8);
+    q[2] = (uint8_t)val;
+  }
+  if (m > 0) *outlen_j = dec_final_group(p, (uint64_t)m, body_end, d, D, fb, flags);
+}
+
+// The messages of at most small_max bytes / characters, one thread each, the
+// grid's threads taking messages in turn (the tile kernel's first work).
+template <int DECODE, class Msgs>
+__device__ __noinline__ void code_short_messages(Msgs ms, int64_t nmsg, int64_t small_max,
+                                                 const uint8_t* table, int64_t* first_bad,
+                                                 int64_t* outlen, uint32_t flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nmsg; j += stride) {
+    const int64_t len = ms.len(j);
+    if (len <= 0 || len > small_max) continue;
+    const Msg m = ms.get(j);
+    if (DECODE) {
+      decode_message(m.src, m.len, m.out, table,
+                     reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j, flags, m.lo,
+                     m.hi);
+    } else {
+      encode_message(m.src, m.len, m.out, table, flags, m.lo, m.hi);
+    }
+  }
+}
+
 // Shared memory of a warp: `stages` input stages, and (decode) two output
 // buffers, used by alternate tiles.
 __host__ __device__ __forceinline__ uint32_t stage_in_bytes(int64_t tile) {
@@ -581,9 +718,7 @@ template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
     k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
                  uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
-                 uint32_t flags, int64_t min_mean_len) {
-  // a packed batch of shorter messages on average is the flat kernel's
-  if (min_mean_len > 0 && msgs.mean_len(nmsg) < min_mean_len) return;
+                 uint32_t flags, int64_t small_max) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
@@ -610,11 +745,10 @@ __global__ void __launch_bounds__(NT)
   const int64_t per = (total + nw - 1) / nw;
   const int64_t t_begin = ((int64_t)blockIdx.x * (NT / 32) + warp) * per;
   const int64_t t_end = tmin<int64_t>(total, t_begin + per);
-  if (t_begin >= t_end) return;
   Msgs ms = msgs;
   ms.prepare(nmsg);
   WalkState& walk = walks[warp];  // used by lane 0
-  if (lane == 0) {
+  if (lane == 0 && t_begin < t_end) {  // the first tiles' copies go out first
     walk.j = owner_of(tile_off, nmsg, t_begin);
     walk_load(walk, ms, tile_off);
     for (uint32_t s = 0; s < S && t_begin + s < t_end; ++s) {
@@ -622,6 +756,10 @@ __global__ void __launch_bounds__(NT)
       issue_tile(meta[warp][s], wbase + s * in_b, &full[warp][s]);
     }
   }
+  // short messages (no tiles) while those copies are in flight
+  if (small_max > 0)
+    code_short_messages<DECODE>(ms, nmsg, small_max, table, first_bad, outlen, flags);
+  if (t_begin >= t_end) return;
 
   bool timed_out = false;
   uint32_t s = 0, phase = 0;
@@ -707,14 +845,14 @@ size_t batch_scratch_bytes(int64_t nmsg) {
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
                           int64_t* tile_off, int64_t tile, void* scratch_parts,
                           int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
-                          uint32_t flags) {
+                          uint32_t flags, int64_t small_max) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
   int64_t* part_out = static_cast<int64_t*>(scratch_parts);
   int64_t* part_tiles = part_out + std::max<int64_t>(nparts, 1);
   if (nparts > 0) {
     k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
-                                                                out_off, tile_off, part_out,
-                                                                part_tiles);
+                                                                small_max, out_off, tile_off,
+                                                                part_out, part_tiles);
     k_scan_parts<<<1, kScanThreads, 0, stream>>>(part_out, part_tiles, nparts);
   }
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
@@ -728,7 +866,7 @@ template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                         int32_t* status, int64_t* first_bad, int64_t* outlen,
                         const BatchConfig& cfg, const DeviceInfo* di, uint32_t flags,
-                        cudaStream_t stream, int64_t min_mean_len) {
+                        cudaStream_t stream, int64_t small_max) {
   const size_t smem = batch_smem_bytes(decode, cfg);
   const void* kernel = decode ? reinterpret_cast<const void*>(k_batch_code<NT, 1, Msgs>)
                               : reinterpret_cast<const void*>(k_batch_code<NT, 0, Msgs>);
@@ -741,11 +879,11 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const uint32_t stages = (uint32_t)cfg.stages;
   if (!decode) {
     k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                          nullptr, nullptr, flags, min_mean_len);
+                                                          nullptr, nullptr, flags, small_max);
     return cudaGetLastError();
   }
   k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                        first_bad, outlen, flags, min_mean_len);
+                                                        first_bad, outlen, flags, small_max);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
@@ -758,20 +896,20 @@ template <class Msgs>
 cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
                             int32_t* status, int64_t* first_bad, int64_t* outlen,
                             const BatchConfig& cfg, uint32_t flags, cudaStream_t stream,
-                            int64_t min_mean_len = 0) {
+                            int64_t small_max = 0) {
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
     case 128:
       return launch_work<128>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, min_mean_len);
+                              flags, stream, small_max);
     case 512:
       return launch_work<512>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, min_mean_len);
+                              flags, stream, small_max);
     default:
       return launch_work<256>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, min_mean_len);
+                              flags, stream, small_max);
   }
 }
 }  // namespace
@@ -791,35 +929,22 @@ cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uin
 }
 
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
+  const int64_t small_max = cfg.kernel == 0 ? batch_small_max(a.decode) : 0;
   cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, cfg.tile,
                                 a.parts, a.decode ? a.first_bad : nullptr,
-                                a.decode ? a.outlen : nullptr, a.stream, a.flags);
+                                a.decode ? a.outlen : nullptr, a.stream, a.flags, small_max);
   if (e != cudaSuccess) return e;
   // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
   PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
-  if (cfg.flat != 2 && flat_eligible(a.decode, a.src, a.dst, a.flags)) {
-    if (cfg.flat == 1) {
-      e = flat_launch(a.decode, a.src, a.in_off, a.dst, a.out_off, a.nmsg, a.first_bad, a.outlen,
-                      default_flat_config(a.decode), a.flags, a.stream);
-      if (e != cudaSuccess || !a.decode) return e;
-      const int64_t blocks = std::max<int64_t>(1, (a.nmsg + 255) / 256);
-      k_batch_decode_finish<PackedMsgs><<<(unsigned)blocks, 256, 0, a.stream>>>(
-          msgs, a.nmsg, a.status, a.first_bad, a.outlen, a.flags);
-      return cudaGetLastError();
-    }
-    // Both kernels are enqueued; each reads the batch's mean message length
-    // on the device and only one of them codes: the flat kernel below the
-    // threshold, the per-warp tile kernel from it on (no host read needed).
-    const int64_t threshold = flat_mean_len_threshold(a.decode);
-    e = flat_launch(a.decode, a.src, a.in_off, a.dst, a.out_off, a.nmsg, a.first_bad, a.outlen,
-                    default_flat_config(a.decode), a.flags, a.stream, threshold);
-    if (e != cudaSuccess) return e;
-    return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen,
-                           cfg, a.flags, a.stream, threshold);
-  }
+  // short messages go one thread each at the start of the tile kernel
   return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen, cfg,
-                         a.flags, a.stream);
+                         a.flags, a.stream, small_max);
 }
+
+// Longest messages (input bytes / characters) coded one thread each by
+// default: below these lengths that is faster on GB300 than a tile per
+// message, and a thread's chain of units stays short next to its tiles.
+int64_t batch_small_max(int decode) { return decode ? 344 : 256; }
 
 int batch_read_and_clear_fault(unsigned int* out) {
   unsigned int v = 0, zero = 0;

@@ -15,9 +15,9 @@ struct BatchConfig {
                       // (decode, multiple of 512) per warp tile
   int blocks_per_sm;  // persistent CTAs per SM at most (0: as many as fit)
   int stages = 4;     // input stages per warp (2..6)
-  int flat = 0;       // aligned packed batches: 0 = the flat kernels when the
-                      // mean message length is short, 1 = always the flat
-                      // kernels, 2 = always the per-warp tile kernels
+  int kernel = 0;     // packed batches: 0 = short messages one thread each and
+                      // the per-warp tile kernels for the rest, 1 = the per-warp
+                      // tile kernels for every message
 };
 
 struct BatchArgs {
@@ -64,9 +64,13 @@ inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** tile_off,
 
 // Output offsets (and tile offsets) of a batch; first_bad/outlen (decode)
 // are initialised when non-null.
+// small_max > 0: messages of at most small_max bytes / characters get no tiles
+// (the short-message kernel codes them).
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
                           int64_t* tile_off, int64_t tile, void* parts, int64_t* first_bad,
-                          int64_t* outlen, cudaStream_t stream, uint32_t flags = 0);
+                          int64_t* outlen, cudaStream_t stream, uint32_t flags = 0,
+                          int64_t small_max = 0);
+int64_t batch_small_max(int decode);
 
 // Offsets + the persistent tile kernel (+ the decode finish kernel).
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);
@@ -79,33 +83,6 @@ constexpr size_t kBatchSmemLimit = 227 * 1024 - 8 * 1024;
 // Dynamic shared memory of a batched launch: per warp, `stages` input
 // stages of a tile (and, decoding, one output buffer).
 size_t batch_smem_bytes(int decode, const BatchConfig& c);
-
-// Shape of the flat kernels (flat.cu), which code a packed batch as one
-// stream: tile = output bytes (encode) or characters (decode) per CTA tile,
-// a multiple of 4096; stages = input stages per CTA (2..6).
-struct FlatConfig {
-  int64_t tile;
-  int stages;
-  int blocks_per_sm;  // 0: as many as fit
-};
-
-// The flat kernels apply to packed batches with padded output and a
-// 16-byte-aligned output buffer (encode) or input buffer (decode).
-bool flat_eligible(int decode, const uint8_t* src, const uint8_t* dst, uint32_t flags);
-bool flat_config_valid(int decode, const FlatConfig& c);
-FlatConfig default_flat_config(int decode);
-size_t flat_smem_bytes(int decode, int64_t tile, int stages);
-
-// The flat encode or decode kernel of a batch whose out_off (and, decode,
-// initial first_bad / outlen) are in place; the decode finish kernel is the
-// caller's.
-// max_mean_len > 0: the kernel returns at once when the batch's mean message
-// length (read on the device) is max_mean_len or more.
-cudaError_t flat_launch(int decode, const uint8_t* src, const int64_t* in_off, uint8_t* dst,
-                        const int64_t* out_off, int64_t nmsg, int64_t* first_bad, int64_t* outlen,
-                        const FlatConfig& cfg, uint32_t flags, cudaStream_t stream,
-                        int64_t max_mean_len = 0);
-int64_t flat_mean_len_threshold(int decode);
 
 // Valid shapes and the defaults used when the tuner has no entry.
 bool batch_config_valid(int decode, const BatchConfig& c);

@@ -12,7 +12,7 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
   if (c.threads != 128 && c.threads != 256 && c.threads != 512) return false;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) return false;
   if (c.stages < 2 || c.stages > 6) return false;
-  if (c.flat < 0 || c.flat > 2) return false;
+  if (c.kernel < 0 || c.kernel > 1) return false;
   const int64_t row = decode ? 512 : 384;  // one unit per lane of a warp
   if (c.tile < row || c.tile > 16 * row || c.tile % row) return false;
   return batch_smem_bytes(decode, c) <= kBatchSmemLimit;

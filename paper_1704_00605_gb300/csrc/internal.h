@@ -68,7 +68,6 @@ cudaError_t decode_ws_launch(const uint8_t* src, uint64_t m, uint8_t* dst, b64_r
 // Reads and clears the fault words of every kernel file (current device).
 int read_and_clear_faults();
 int batch_read_and_clear_fault(unsigned int* out);
-int flat_read_and_clear_fault(unsigned int* out);
 int single_read_and_clear_fault(unsigned int* out);
 
 }  // namespace gb64

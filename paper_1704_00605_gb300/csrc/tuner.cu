@@ -60,7 +60,7 @@ void load_env_once_locked() {
 BatchConfig batch_config_of(const b64_shape& s) {
   BatchConfig c{s.threads, s.tile, s.blocks_per_sm};
   c.stages = s.stages ? s.stages : 4;
-  c.flat = s.units_per_thread;  // batch kinds: the kernel choice
+  c.kernel = s.units_per_thread;  // batch kinds: the kernel choice
   return c;
 }
 
@@ -212,7 +212,7 @@ int b64_shape_get(int kind, int64_t total, int64_t nmsg, b64_shape* out) {
                      (int64_t)c.threads * c.upt * unit, 0.f};
   } else {
     const BatchConfig c = tuned_batch_config(kind == kBatchDecode, nmsg, total);
-    *out = b64_shape{c.threads, c.flat, c.stages, c.blocks_per_sm, c.tile, 0.f};
+    *out = b64_shape{c.threads, c.kernel, c.stages, c.blocks_per_sm, c.tile, 0.f};
   }
   return B64_OK;
 }

@@ -1,8 +1,8 @@
-"""Both kernels of the batched codec against the oracle (exact), on the same
-batches: the flat whole-batch kernels and the per-warp tile kernels, each
-forced through the shape table's kernel choice (1 = flat, 2 = per-warp) and,
-for the per-warp kernels, also reached through buffers that do not start on
-a 16-byte boundary. Batches mix empty, tiny and large messages, lengths of
+"""The kernels of the batched codec against the oracle (exact), on the same
+batches: the default (short messages one thread each, the per-warp tile
+kernels for the rest) and the per-warp tile kernels for every message,
+chosen through the shape table's kernel choice (0, 1), each with buffers on
+and off a 16-byte boundary. Batches mix empty, tiny and large messages, lengths of
 every class mod 3 and mod 4, messages that straddle tiles and tiles that
 hold hundreds of messages, padding, errors at every kind of position, and
 the decode flags."""
@@ -16,7 +16,7 @@ from paper_1704_00605_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 URL, NOPAD, STRICT = 1, 2, 4
-FLAT, PER_WARP = 1, 2
+DEFAULT, PER_WARP = 0, 1
 
 
 @contextlib.contextmanager
@@ -113,9 +113,9 @@ def test_encode_both_paths(gb64, oracle, seed):
     exp, exp_off = oracle.encode_batch(data, off)
     exp_url = np.concatenate([oracle.encode_ex(data[off[j]:off[j + 1]], URL)
                               for j in range(off.size - 1)])
-    for mode in (FLAT, PER_WARP):
+    for mode in (DEFAULT, PER_WARP):
         with kernel_choice(gb64, mode):
-            for shift in (0, 4, 8, 12, 1):  # shifted outputs: the per-warp kernel
+            for shift in (0, 4, 8, 12, 1):  # outputs on and off a 16-byte boundary
                 out, out_off = _encode(gb64, data, off, shift)
                 assert np.array_equal(out_off, exp_off)
                 assert np.array_equal(out, exp), (mode, shift)
@@ -142,17 +142,16 @@ def test_decode_both_paths_valid_and_errors(gb64, oracle, seed):
             chars[p] = NON_ALPHABET_NON_PAD[int(rng.integers(0, NON_ALPHABET_NON_PAD.size))]
             nbad += 1
     assert nbad > 10
-    for mode in (FLAT, PER_WARP):
+    for mode in (DEFAULT, PER_WARP):
         with kernel_choice(gb64, mode):
-            for shift in (0, 3, 8):  # shifted inputs: the per-warp kernel
+            for shift in (0, 3, 8):  # inputs on and off a 16-byte boundary
                 _check_decode(oracle, chars, coff, _decode(gb64, chars, coff, shift), 0)
 
 
 @pytest.mark.parametrize("flags", [0, URL, NOPAD, STRICT, URL | NOPAD | STRICT])
 def test_decode_both_paths_lengths_not_multiple_of_4(gb64, oracle, flags):
     """Messages of every length mod 4 (so later messages start off a
-    multiple of 4 and the flat kernel codes them quad by quad), with random
-    '=' and other bytes mixed in."""
+    multiple of 4), with random '=' and other bytes mixed in."""
     rng = np.random.default_rng(7 + flags)
     alpha = oracle.encode_ex(np.frombuffer(int("".join(f"{v:06b}" for v in range(64)), 2)
                                            .to_bytes(48, "big"), dtype=np.uint8), flags & URL)
@@ -169,21 +168,21 @@ def test_decode_both_paths_lengths_not_multiple_of_4(gb64, oracle, flags):
             chars[b - 1] = 0x3D
         elif b > a and r < 0.4:
             chars[int(rng.integers(a, b))] = int(rng.integers(0, 256))
-    for mode in (FLAT, PER_WARP):
+    for mode in (DEFAULT, PER_WARP):
         with kernel_choice(gb64, mode):
             for shift in (0, 5):
                 _check_decode(oracle, chars, off, _decode(gb64, chars, off, shift, flags), flags)
 
 
 def test_decode_tiles_of_tiny_messages(gb64, oracle):
-    """100,000 messages of 0-24 characters: flat tiles of hundreds of
-    messages, every final group and padding form."""
+    """100,000 messages of 0-24 characters (one thread each): every final
+    group and padding form, buffers on and off a 16-byte boundary."""
     rng = np.random.default_rng(11)
     lens = rng.integers(0, 19, 100_000)
     off = W.offsets_from_lengths(lens.astype(np.int64))
     data = W.uniform_bytes(int(off[-1]), 12)
     chars, coff = oracle.encode_batch(data, off)
-    for shift in (0, 1):  # by mean length: the flat kernel, then the per-warp kernel
+    for shift in (0, 1):
         res = _decode(gb64, chars, coff, shift)
         h, oo, st, fb, ol = res
         assert (st == 0).all() and np.array_equal(ol, np.diff(off))
@@ -193,10 +192,10 @@ def test_decode_tiles_of_tiny_messages(gb64, oracle):
     assert np.array_equal(out, chars) and np.array_equal(out_off, coff)
 
 
-def test_kernel_choice_by_mean_length(gb64, oracle):
-    """The default choice: the same batch content cut into short messages
-    (the flat kernels) and into long ones (the per-warp kernels) codes
-    exactly; a batch of mostly tiny messages with a few large ones too."""
+def test_mixed_short_and_long_batches(gb64, oracle):
+    """The same content cut into short messages (one thread each) and into
+    long ones (the tile kernels), and a batch of mostly tiny messages with a
+    few large ones, code exactly by default."""
     rng = np.random.default_rng(13)
     data = W.uniform_bytes(3 << 20, 14)
     for lens in (rng.integers(0, 200, 40_000), rng.integers(5000, 60000, 100),
@@ -208,3 +207,32 @@ def test_kernel_choice_by_mean_length(gb64, oracle):
         out, out_off = _encode(gb64, d, off, 0)
         assert np.array_equal(out_off, exp_off) and np.array_equal(out, exp)
         _check_decode(oracle, exp, exp_off, _decode(gb64, exp, exp_off, 0), 0)
+
+
+@pytest.mark.parametrize("flags", [0, URL | NOPAD, STRICT])
+def test_lengths_around_the_short_message_limit(gb64, oracle, flags):
+    """Messages just below, at and above the longest length the short-message
+    kernel takes (256 bytes, 344 characters), mixed with tiny and long ones,
+    with errors: both sides of the split code exactly."""
+    from paper_1704_00605_gb300.workloads import NON_ALPHABET_NON_PAD
+
+    rng = np.random.default_rng(31 + flags)
+    lens = np.concatenate([rng.integers(230, 290, 600), rng.integers(0, 40, 300),
+                           rng.integers(250, 262, 300), rng.integers(250, 260, 200),
+                           [5000, 70000, 0, 1, 2]])
+    rng.shuffle(lens)
+    off = W.offsets_from_lengths(lens.astype(np.int64))
+    data = W.uniform_bytes(int(off[-1]), 60 + flags)
+    enc = [oracle.encode_ex(data[off[j]:off[j + 1]], flags & (URL | NOPAD)) for j in range(off.size - 1)]
+    if not flags & NOPAD:
+        out, out_off = _encode(gb64, data, off, 0, flags & URL)
+        assert np.array_equal(out, np.concatenate(enc))
+    chars = [e.copy() for e in enc]
+    for j in rng.integers(0, len(chars), 60):
+        if chars[j].size:
+            chars[j][int(rng.integers(0, chars[j].size))] = NON_ALPHABET_NON_PAD[int(rng.integers(0, 191))]
+    coff = W.offsets_from_lengths(np.array([c.size for c in chars], dtype=np.int64))
+    allc = np.concatenate(chars)
+    for mode in (DEFAULT, PER_WARP):
+        with kernel_choice(gb64, mode):
+            _check_decode(oracle, allc, coff, _decode(gb64, allc, coff, 0, flags), flags)

@@ -69,7 +69,8 @@ def test_tune_batch_and_every_candidate_is_exact(gb64, oracle, restore_shapes, k
     exp_enc, exp_off = oracle.encode_batch(data, off)
     src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
     for t in trials:
-        shape = dict(threads=t["threads"], tile=t["tile"], blocks_per_sm=t["blocks_per_sm"])
+        shape = dict(threads=t["threads"], tile=t["tile"], blocks_per_sm=t["blocks_per_sm"],
+                     stages=t["stages"], units_per_thread=t["units_per_thread"])
         if kind == 2:
             gb64.b64_shape_set(2, total, nmsg, **shape)
         else:
