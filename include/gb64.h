@@ -125,7 +125,7 @@ int b64_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg, uint8
  * the call (a fixed memory budget or an allocator owned by someone else, or
  * a hot path that cannot afford cudaMalloc/cudaFree synchronizing the
  * device). Same arguments, kernels and results as b64_decode_batch, but the
- * scratch lives in a fixed array inside the library (about 576 KiB per GPU
+ * scratch lives in a fixed array inside the library (about 1 MiB per GPU
  * that uses it, held until the process exits) instead of coming from the
  * stream-ordered allocator. At most 65536 messages per call; a larger nmsg
  * returns B64_ERR_ARG with nothing enqueued. Every call on a device shares
@@ -148,16 +148,17 @@ enum {
 /* A launch shape. Single kinds use threads, units_per_thread (12 input
  * bytes or 16 characters each; tile = threads * units_per_thread * unit),
  * stages (TMA stages in shared memory) and blocks_per_sm (0 = as many as
- * fit). Batch kinds use threads, tile (input bytes per warp tile, a
- * multiple of 384 up to 6144, or characters, a multiple of 512 up to
- * 8192), stages (input stages per warp, 2..6; 0 = 4) and blocks_per_sm
- * (0 = as many as fit) of the per-warp tile kernels; the shape's shared
- * memory, threads / 32 * (stages * (tile + 32) + (decode only)
- * 3 * tile / 4 + 32) bytes, must stay within 219 KiB. For batch kinds
- * units_per_thread selects the kernels of packed batches: 0 = messages of
- * up to 256 bytes (encode) or 344 characters (decode) one thread each and
- * the per-warp tile kernels for the longer ones, 1 = the per-warp tile
- * kernels for every message. ms is a measured time. */
+ * fit). Batch kinds use units_per_thread as the kernel choice: 0 = messages
+ * of up to 256 bytes (encode) or 344 characters (decode) one thread each
+ * and per-warp tiles staged in shared memory for the longer ones, 1 =
+ * staged tiles for every message, 2 = short messages one thread each and
+ * unstaged tiles (read and written straight from and to global memory) for
+ * the rest. Then threads, tile (input bytes per warp tile, a multiple of
+ * 384, or characters, a multiple of 512: up to 16 such rows staged, 64
+ * unstaged), stages (staged input stages per warp, 2..6; 0 = 4) and
+ * blocks_per_sm (0 = as many as fit); a staged shape's shared memory,
+ * threads / 32 * (stages * (tile + 32) + (decode only) 3 * tile / 4 + 32)
+ * bytes, must stay within 219 KiB. ms is a measured time. */
 typedef struct {
   int32_t threads;
   int32_t units_per_thread;

@@ -32,148 +32,230 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int64_t kScanPerBlock = (int64_t)kScanThreads * kScanItems;
 constexpr int64_t kNoBad = INT64_MAX;
+constexpr int64_t kTileCost = kBatchTileCost;
 
 // ----------------------------------------------------------------- scan
-// Output length and tile count of one message; messages of at most
-// small_max bytes get no tiles (the short-message kernel codes them).
+// Output length, tile count and weight of one message; messages of at most
+// small_max bytes get no tiles (threads code them one each) and no weight.
+// A message's weight, its length plus kTileCost per tile, is what the
+// tile kernels divide evenly among their warps.
 __device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, uint32_t flags,
-                                           int64_t small_max, int64_t& outv, int64_t& tiles) {
+                                           int64_t small_max, int64_t& outv, int64_t& tiles,
+                                           int64_t& weight) {
   if (len < 0) len = 0;
   outv = decode ? (int64_t)decoded_cap_flags((uint64_t)len, flags)
                 : (int64_t)encoded_len_flags((uint64_t)len, flags);
   tiles = len > small_max ? (len + tile - 1) / tile : 0;
+  weight = tiles ? len + tiles * kTileCost : 0;
 }
 
-// Block-wide exclusive scan of a pair of int64 values; returns the block total.
-__device__ __forceinline__ void block_exclusive_scan2(int64_t& a, int64_t& b, int64_t& tot_a,
-                                                      int64_t& tot_b) {
-  __shared__ int64_t wa[kScanThreads / 32], wb[kScanThreads / 32];
+// Three int64 running sums (output, tiles, weight).
+struct Sum3 {
+  int64_t v[3];
+};
+
+__device__ __forceinline__ Sum3 shfl_up3(const Sum3& x, int d) {
+  Sum3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) r.v[i] = __shfl_up_sync(0xFFFFFFFFu, x.v[i], d);
+  return r;
+}
+
+// Block-wide exclusive scan of x; tot receives the block total.
+__device__ __forceinline__ void block_exclusive_scan3(Sum3& x, Sum3& tot) {
+  __shared__ int64_t ws[3][kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t ia = a, ib = b;  // inclusive within the warp
+  Sum3 inc = x;  // inclusive within the warp
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const int64_t xa = __shfl_up_sync(0xFFFFFFFFu, ia, d);
-    const int64_t xb = __shfl_up_sync(0xFFFFFFFFu, ib, d);
-    if (lane >= d) {
-      ia += xa;
-      ib += xb;
-    }
+    const Sum3 y = shfl_up3(inc, d);
+    if (lane >= d)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) inc.v[i] += y.v[i];
   }
-  if (lane == 31) {
-    wa[warp] = ia;
-    wb[warp] = ib;
-  }
+  if (lane == 31)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ws[i][warp] = inc.v[i];
   __syncthreads();
   if (warp == 0) {
-    int64_t sa = lane < kScanThreads / 32 ? wa[lane] : 0;
-    int64_t sb = lane < kScanThreads / 32 ? wb[lane] : 0;
+    Sum3 w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w.v[i] = lane < kScanThreads / 32 ? ws[i][lane] : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const int64_t xa = __shfl_up_sync(0xFFFFFFFFu, sa, d);
-      const int64_t xb = __shfl_up_sync(0xFFFFFFFFu, sb, d);
-      if (lane >= d) {
-        sa += xa;
-        sb += xb;
-      }
+      const Sum3 y = shfl_up3(w, d);
+      if (lane >= d)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w.v[i] += y.v[i];
     }
-    if (lane < kScanThreads / 32) {
-      wa[lane] = sa;  // inclusive over warps
-      wb[lane] = sb;
-    }
+    if (lane < kScanThreads / 32)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ws[i][lane] = w.v[i];  // inclusive over warps
   }
   __syncthreads();
-  const int64_t pa = warp ? wa[warp - 1] : 0, pb = warp ? wb[warp - 1] : 0;
-  tot_a = wa[kScanThreads / 32 - 1];
-  tot_b = wb[kScanThreads / 32 - 1];
-  a = pa + ia - a;
-  b = pb + ib - b;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int64_t before = warp ? ws[i][warp - 1] : 0;
+    tot.v[i] = ws[i][kScanThreads / 32 - 1];
+    x.v[i] = before + inc.v[i] - x.v[i];
+  }
 }
 
+// The block totals: parts[i * nparts + p] for sum i of block p.
 __global__ void __launch_bounds__(kScanThreads)
     k_scan_local(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
                  uint32_t flags, int64_t small_max, int64_t* __restrict__ out_off,
-                 int64_t* __restrict__ tile_off, int64_t* __restrict__ part_out,
-                 int64_t* __restrict__ part_tiles) {
+                 int64_t* __restrict__ tile_off, int64_t* __restrict__ weight_off,
+                 int64_t* __restrict__ parts, int64_t nparts) {
   const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
-  int64_t vo[kScanItems], vt[kScanItems];
-  int64_t so = 0, st = 0;
+  Sum3 item[kScanItems];
+  Sum3 sum = {{0, 0, 0}};
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t j = base + i;
-    vo[i] = vt[i] = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t j = base + k;
+    item[k] = Sum3{{0, 0, 0}};
     if (j < nmsg)
-      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, vo[i], vt[i]);
-    so += vo[i];
-    st += vt[i];
-  }
-  int64_t eo = so, et = st, to, tt;
-  block_exclusive_scan2(eo, et, to, tt);
+      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, item[k].v[0],
+                 item[k].v[1], item[k].v[2]);
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t j = base + i;
-    eo += vo[i];
-    et += vt[i];
-    if (j < nmsg) {
-      out_off[j + 1] = eo;  // inclusive within the block; k_scan_add adds the block base
-      tile_off[j + 1] = et;
+    for (int i = 0; i < 3; ++i) sum.v[i] += item[k].v[i];
+  }
+  Sum3 tot;
+  block_exclusive_scan3(sum, tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t j = base + k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sum.v[i] += item[k].v[i];
+    if (j < nmsg) {  // inclusive within the block; k_scan_add adds the block base
+      out_off[j + 1] = sum.v[0];
+      tile_off[j + 1] = sum.v[1];
+      weight_off[j + 1] = sum.v[2];
     }
   }
-  if (threadIdx.x == 0) {
-    part_out[blockIdx.x] = to;
-    part_tiles[blockIdx.x] = tt;
-  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) parts[i * nparts + blockIdx.x] = tot.v[i];
 }
 
 // One CTA: exclusive scan of the block totals, in place.
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_parts(int64_t* __restrict__ part_out, int64_t* __restrict__ part_tiles, int64_t nparts) {
-  __shared__ int64_t carry_o, carry_t;
-  if (threadIdx.x == 0) carry_o = carry_t = 0;
+    k_scan_parts(int64_t* __restrict__ parts, int64_t nparts) {
+  __shared__ int64_t carry[3];
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t c = 0; c < nparts; c += kScanThreads) {
-    const int64_t i = c + threadIdx.x;
-    int64_t a = i < nparts ? part_out[i] : 0, b = i < nparts ? part_tiles[i] : 0;
-    int64_t ta, tb;
-    block_exclusive_scan2(a, b, ta, tb);
-    if (i < nparts) {
-      part_out[i] = a + carry_o;
-      part_tiles[i] = b + carry_t;
-    }
+    const int64_t p = c + threadIdx.x;
+    Sum3 x;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x.v[i] = p < nparts ? parts[i * nparts + p] : 0;
+    Sum3 tot;
+    block_exclusive_scan3(x, tot);
+    if (p < nparts)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) parts[i * nparts + p] = x.v[i] + carry[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      carry_o += ta;
-      carry_t += tb;
-    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) carry[i] += tot.v[i];
     __syncthreads();
   }
 }
 
 __global__ void k_scan_add(int64_t nmsg, int64_t* __restrict__ out_off,
-                           int64_t* __restrict__ tile_off, const int64_t* __restrict__ part_out,
-                           const int64_t* __restrict__ part_tiles, int64_t* __restrict__ first_bad,
-                           int64_t* __restrict__ outlen) {
+                           int64_t* __restrict__ tile_off, int64_t* __restrict__ weight_off,
+                           const int64_t* __restrict__ parts, int64_t nparts,
+                           int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) {
     out_off[0] = 0;
     tile_off[0] = 0;
+    weight_off[0] = 0;
   }
   if (j >= nmsg) return;
   const int64_t p = j / kScanPerBlock;
-  out_off[j + 1] += part_out[p];
-  tile_off[j + 1] += part_tiles[p];
+  out_off[j + 1] += parts[p];
+  tile_off[j + 1] += parts[nparts + p];
+  weight_off[j + 1] += parts[2 * nparts + p];
   if (first_bad) first_bad[j] = kNoBad;
   if (outlen) outlen[j] = 0;
 }
 
 // ------------------------------------------------------------ tile walk
-// Largest j in [0, nmsg) with tile_off[j] <= t (tile_off non-decreasing).
-__device__ __forceinline__ int64_t owner_of(const int64_t* tile_off, int64_t nmsg, int64_t t) {
+// Largest j in [0, nmsg) with tile_off[j] <= t (tile_off non-decreasing,
+// t < tile_off[nmsg]). The whole warp searches: each round its 32 lanes
+// probe 32 evenly spaced offsets and the count of those <= t narrows the
+// interval 33-fold (4 dependent loads for 10^5 messages, not 17).
+__device__ __forceinline__ int64_t owner_of_warp(const int64_t* tile_off, int64_t nmsg, int64_t t,
+                                                 uint32_t lane) {
   int64_t lo = 0, hi = nmsg;  // invariant: tile_off[lo] <= t < tile_off[hi]
   while (hi - lo > 1) {
-    const int64_t mid = lo + (hi - lo) / 2;
-    if (__ldg(tile_off + mid) <= t) lo = mid; else hi = mid;
+    const int64_t span = hi - lo;
+    // probes lo < p_0 <= p_1 <= ... <= p_31 < hi
+    const int64_t p = lo + 1 + (span - 1) * (int64_t)lane / 32;
+    const uint32_t le = __ballot_sync(0xFFFFFFFFu, __ldg(tile_off + p) <= t);
+    const int c = __popc(le);  // the probes <= t are lanes [0, c)
+    const int64_t below = __shfl_sync(0xFFFFFFFFu, p, c > 0 ? c - 1 : 0);
+    const int64_t above = __shfl_sync(0xFFFFFFFFu, p, c < 32 ? c : 31);
+    if (c > 0) lo = below;
+    if (c < 32) hi = above;
   }
   return lo;
+}
+
+// The same search for two targets at once: lanes 0-15 find the owner of
+// their x, lanes 16-31 of theirs (16 probes a round each).
+__device__ __forceinline__ int64_t owner_of_halves(const int64_t* off, int64_t nmsg, int64_t x,
+                                                   uint32_t lane) {
+  const uint32_t h = lane >> 4, k = lane & 15u;
+  int64_t lo = 0, hi = nmsg;  // invariant: off[lo] <= x < off[hi]
+  while (__any_sync(0xFFFFFFFFu, hi - lo > 1)) {
+    const int64_t span = hi - lo;
+    // probes lo < p_0 <= ... <= p_15 < hi (p = hi <= nmsg once span is 1)
+    const int64_t p = lo + 1 + (span - 1) * (int64_t)k / 16;
+    const uint32_t le = __ballot_sync(0xFFFFFFFFu, __ldg(off + p) <= x);
+    const int c = __popc((le >> (16u * h)) & 0xFFFFu);
+    const int64_t below = __shfl_sync(0xFFFFFFFFu, p, (int)(16u * h) + (c > 0 ? c - 1 : 0));
+    const int64_t above = __shfl_sync(0xFFFFFFFFu, p, (int)(16u * h) + (c < 16 ? c : 15));
+    if (span > 1) {
+      if (c > 0) lo = below;
+      if (c < 16) hi = above;
+    }
+  }
+  return lo;
+}
+
+// The tiles [t_begin, t_end) of warp w of the grid's nw warps. With weight
+// offsets the warps split the total weight evenly, a warp taking the tiles
+// that start (tile k of message j starts at weight_off[j] + k * (tile +
+// kTileCost)) in its share: tiles of one message are equal but the last, and
+// messages differ, so equal tile counts would not be equal work. Without
+// them (host-built descriptor batches) every warp gets the same count.
+// j_begin: a message at or before the one holding t_begin (the walk moves
+// forward from it), when t_begin < t_end.
+__device__ __forceinline__ void warp_tile_range(const int64_t* tile_off, const int64_t* weight_off,
+                                                int64_t nmsg, int64_t tile, int64_t w, int64_t nw,
+                                                uint32_t lane, int64_t& t_begin, int64_t& t_end,
+                                                int64_t& j_begin) {
+  const int64_t total = __ldg(tile_off + nmsg);
+  if (!weight_off || total == 0) {
+    const int64_t per = (total + nw - 1) / nw;
+    t_begin = tmin<int64_t>(total, w * per);
+    t_end = tmin<int64_t>(total, t_begin + per);
+    j_begin = t_begin < t_end ? owner_of_warp(tile_off, nmsg, t_begin, lane) : 0;
+    return;
+  }
+  const int64_t wt = __ldg(weight_off + nmsg);  // > 0 when there are tiles
+  const bool last = w + 1 == nw;
+  // lanes 0-15: the start of the share, 16-31: its end (the next share's start)
+  const int64_t x = lane < 16 ? wt * w / nw : (last ? 0 : wt * (w + 1) / nw);
+  const int64_t j = owner_of_halves(weight_off, nmsg, x, lane);
+  const int64_t t0 = __ldg(tile_off + j), nt = __ldg(tile_off + j + 1) - t0;
+  const int64_t k = (x - __ldg(weight_off + j) + tile + kTileCost - 1) / (tile + kTileCost);
+  const int64_t t = t0 + tmin<int64_t>(k, nt);  // the first tile starting at or after x
+  t_begin = __shfl_sync(0xFFFFFFFFu, t, 0);
+  t_end = last ? total : __shfl_sync(0xFFFFFFFFu, t, 16);
+  j_begin = __shfl_sync(0xFFFFFFFFu, j, 0);  // t_begin is in j or a later message
 }
 
 // One message as a tile sees it: its bytes, its output, and the bounds that
@@ -360,6 +442,41 @@ __device__ __forceinline__ void enc_chunks(const uint8_t* sb, uint8_t* db, int32
   }
 }
 
+// The same chunks read straight from global memory (no staging): s is the
+// input of the first chunk, s + 12i is R mod 4 for every i, and the aligned
+// words covering each chunk's 12 bytes lie inside the input buffer. Each
+// lane issues the loads of up to four chunks before coding them.
+template <int R>
+__device__ __forceinline__ void enc_chunks_global(const uint8_t* s, uint8_t* db, int32_t cnt,
+                                                  uint32_t lane, const uint8_t* T) {
+  constexpr int32_t kAhead = 4;
+  const uint32_t* wb = reinterpret_cast<const uint32_t*>(s - R);
+  for (int32_t i0 = 0; i0 < cnt; i0 += 32 * kAhead) {
+    uint32_t q[kAhead][4];
+#pragma unroll
+    for (int32_t k = 0; k < kAhead; ++k) {
+      const int32_t i = i0 + 32 * k + (int32_t)lane;
+      if (i < cnt) {
+        const uint32_t* p = wb + 3 * i;
+        q[k][0] = __ldg(p);
+        q[k][1] = __ldg(p + 1);
+        q[k][2] = __ldg(p + 2);
+        q[k][3] = R ? __ldg(p + 3) : 0u;
+      }
+    }
+#pragma unroll
+    for (int32_t k = 0; k < kAhead; ++k) {
+      const int32_t i = i0 + 32 * k + (int32_t)lane;
+      if (i < cnt) {
+        const uint32_t x = R ? __funnelshift_r(q[k][0], q[k][1], 8 * R) : q[k][0];
+        const uint32_t y = R ? __funnelshift_r(q[k][1], q[k][2], 8 * R) : q[k][1];
+        const uint32_t z = R ? __funnelshift_r(q[k][2], q[k][3], 8 * R) : q[k][2];
+        st_global_v4_cs(db + 16 * i, enc_unit(x, y, z, T));
+      }
+    }
+  }
+}
+
 // Encodes one tile (Algorithm 1 per 12-byte unit) straight to global memory
 // in aligned 16-byte stores; the message's last tile also codes the partial
 // group with its padding.
@@ -372,6 +489,8 @@ __device__ __forceinline__ void enc_chunks(const uint8_t* sb, uint8_t* db, int32
 //  - Otherwise (d mod 4 != 0): lanes code units, and the lane of unit u
 //    builds aligned chunk u from unit u - 1 (the previous lane, or the
 //    previous row's last lane) and unit u; the ends go out as bytes.
+// DIRECT: nothing was staged (v.ia == v.ib); whole chunks read global memory.
+template <bool DIRECT>
 __device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in,
                                             const uint8_t* T, uint32_t lane, uint32_t flags) {
   const uint32_t nu = v.len / 12u;
@@ -385,19 +504,46 @@ __device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in
     // p0 + 12c; those whose 12 bytes were all copied, [c_lo, c_hi), take
     // the loop specialised on the stage's 4-byte phase
     const int32_t cf = q ? 1 : 0, n = (int32_t)nu;
-    const int32_t p0 = (int32_t)v.o - 3 * (int32_t)q;
-    const int32_t c_lo = n > 0 ? min(n, max(cf, ((int32_t)v.ia - p0 + 11) / 12)) : 0;
-    const int32_t room = (int32_t)v.ib - 12 - p0;  // last copied chunk start
-    const int32_t c_hi = room < 0 ? c_lo : max(c_lo, min(n, room / 12 + 1));
-    if (c_hi > c_lo) {
-      const uint8_t* sb = in + (p0 + 12 * c_lo);
-      uint8_t* db = abase + 16u * (uint32_t)c_lo;
-      const int32_t cnt = c_hi - c_lo;
-      switch ((p0 + 12 * c_lo) & 3) {
-        case 0: enc_chunks<0>(sb, db, cnt, lane, T); break;
-        case 1: enc_chunks<1>(sb, db, cnt, lane, T); break;
-        case 2: enc_chunks<2>(sb, db, cnt, lane, T); break;
-        default: enc_chunks<3>(sb, db, cnt, lane, T); break;
+    int32_t c_lo, c_hi;
+    if (DIRECT) {
+      // every whole chunk, but a chunk whose aligned words would reach
+      // outside the input buffer (first or last only) goes with the edges
+      c_lo = min(n, cf);
+      c_hi = n;
+      const uintptr_t s0 = reinterpret_cast<uintptr_t>(sp) + 12 * c_lo - 3 * q;
+      const uint32_t r = (uint32_t)(s0 & 3u);
+      if (r && c_hi > c_lo) {
+        if (s0 - r < reinterpret_cast<uintptr_t>(v.lo)) ++c_lo;
+        const uintptr_t sl = reinterpret_cast<uintptr_t>(sp) + 12 * (c_hi - 1) - 3 * q;
+        if (sl - r + 16 > reinterpret_cast<uintptr_t>(v.hi)) --c_hi;
+        c_hi = max(c_hi, c_lo);
+      }
+      if (c_hi > c_lo) {
+        const uint8_t* s = sp + (12 * c_lo - 3 * (int32_t)q);
+        uint8_t* db = abase + 16u * (uint32_t)c_lo;
+        const int32_t cnt = c_hi - c_lo;
+        switch (r) {
+          case 0: enc_chunks_global<0>(s, db, cnt, lane, T); break;
+          case 1: enc_chunks_global<1>(s, db, cnt, lane, T); break;
+          case 2: enc_chunks_global<2>(s, db, cnt, lane, T); break;
+          default: enc_chunks_global<3>(s, db, cnt, lane, T); break;
+        }
+      }
+    } else {
+      const int32_t p0 = (int32_t)v.o - 3 * (int32_t)q;
+      c_lo = n > 0 ? min(n, max(cf, ((int32_t)v.ia - p0 + 11) / 12)) : 0;
+      const int32_t room = (int32_t)v.ib - 12 - p0;  // last copied chunk start
+      c_hi = room < 0 ? c_lo : max(c_lo, min(n, room / 12 + 1));
+      if (c_hi > c_lo) {
+        const uint8_t* sb = in + (p0 + 12 * c_lo);
+        uint8_t* db = abase + 16u * (uint32_t)c_lo;
+        const int32_t cnt = c_hi - c_lo;
+        switch ((p0 + 12 * c_lo) & 3) {
+          case 0: enc_chunks<0>(sb, db, cnt, lane, T); break;
+          case 1: enc_chunks<1>(sb, db, cnt, lane, T); break;
+          case 2: enc_chunks<2>(sb, db, cnt, lane, T); break;
+          default: enc_chunks<3>(sb, db, cnt, lane, T); break;
+        }
       }
     }
     // the rest: chunks outside the copied part, and with q > 0 the partial
@@ -506,9 +652,46 @@ __device__ __forceinline__ void dec_store_row(uint8_t* out, uint32_t o2, uint32_
   carry = __shfl_sync(0xFFFFFFFFu, o.z, 31);
 }
 
+// The same row written straight to the tile's output d (unit u at
+// d + 12u): aligned word stores, the word shared with the unit before the
+// tile and the one shared with the unit after it by bytes (other warps may
+// be writing the rest of those words).
+__device__ __forceinline__ void dec_store_row_global(uint8_t* d, uint32_t u, uint32_t nu, uint3 o,
+                                                     uint32_t& carry, uint32_t lane) {
+  const uint32_t r2 = (uint32_t)(reinterpret_cast<uintptr_t>(d) & 3u);
+  if (r2 == 0) {
+    if (u < nu) {
+      uint32_t* wq = reinterpret_cast<uint32_t*>(d + 12u * u);
+      wq[0] = o.x;
+      wq[1] = o.y;
+      wq[2] = o.z;
+    }
+    return;
+  }
+  uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, o.z, 1);
+  if (lane == 0) prev = carry;
+  if (u < nu) {
+    uint8_t* q = d + 12u * u;
+    uint32_t* wq = reinterpret_cast<uint32_t*>(q - r2);  // aligned word holding q[0]
+    const uint32_t sh = 8u * (4u - r2);
+    if (u == 0) {
+      for (uint32_t k = 0; k < 4u - r2; ++k) q[k] = (uint8_t)(o.x >> (8u * k));
+    } else {
+      wq[0] = __funnelshift_r(prev, o.x, sh);
+    }
+    wq[1] = __funnelshift_r(o.x, o.y, sh);
+    wq[2] = __funnelshift_r(o.y, o.z, sh);
+    if (u == nu - 1)
+      for (uint32_t k = 0; k < r2; ++k) q[12u - r2 + k] = (uint8_t)(o.z >> (sh + 8u * k));
+  }
+  carry = __shfl_sync(0xFFFFFFFFu, o.z, 31);
+}
+
 // Decodes one tile (Algorithm 2 per 16-character unit; whole quads after
 // the last unit and, in the tile holding it, the message's final group go
-// straight to global memory).
+// straight to global memory). DIRECT: the units are read from and written
+// to global memory, four rows' loads issued before their decoding.
+template <bool DIRECT>
 __device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in, uint8_t* out,
                                             const uint8_t* D, unsigned long long* fb,
                                             int64_t* outlen_j, uint32_t lane, uint32_t flags) {
@@ -521,14 +704,38 @@ __device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in
   const uint32_t o2 = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15u);
   unsigned long long bad = ~0ull;
   uint32_t carry = 0;  // last word of the previous row's last unit
-  for (uint32_t base = 0; base < nu; base += 32u) {
-    const uint32_t u = base + lane;
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    if (u < nu) w = dec_load(v, in, u);
-    uint32_t err = 0;
-    const uint3 o = dec_unit(w, D, err);
-    if ((err & kBadFlag) && u < nu && bad == ~0ull) bad = t0 + 16u * u + dec_unit_first_bad(w, D);
-    dec_store_row(out, o2, u, nu, o, carry, lane);
+  if (DIRECT) {
+    constexpr uint32_t kAhead = 4;
+    const uint8_t* s = v.msrc + v.t0;
+    for (uint32_t base = 0; base < nu; base += 32u * kAhead) {
+      uint4 w[kAhead];
+#pragma unroll
+      for (uint32_t k = 0; k < kAhead; ++k) {
+        const uint32_t u = base + 32u * k + lane;
+        w[k] = u < nu ? load16_any(s + 16u * u, v.lo, v.hi) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < kAhead; ++k) {
+        if (base + 32u * k >= nu) break;  // the whole warp
+        const uint32_t u = base + 32u * k + lane;
+        uint32_t err = 0;
+        const uint3 o = dec_unit(w[k], D, err);
+        if ((err & kBadFlag) && u < nu && bad == ~0ull)
+          bad = t0 + 16u * u + dec_unit_first_bad(w[k], D);
+        dec_store_row_global(dp, u, nu, o, carry, lane);
+      }
+    }
+  } else {
+    for (uint32_t base = 0; base < nu; base += 32u) {
+      const uint32_t u = base + lane;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (u < nu) w = dec_load(v, in, u);
+      uint32_t err = 0;
+      const uint3 o = dec_unit(w, D, err);
+      if ((err & kBadFlag) && u < nu && bad == ~0ull)
+        bad = t0 + 16u * u + dec_unit_first_bad(w, D);
+      dec_store_row(out, o2, u, nu, o, carry, lane);
+    }
   }
   warp_min_to(fb, bad);
   const uint32_t nq = (body - 16u * nu) / 4u;
@@ -554,9 +761,11 @@ __device__ __forceinline__ void decode_tile(const TileView& v, const uint8_t* in
   }
   if (lane == 31 && body_end >= t0 && body_end < t0 + v.len)
     *outlen_j = dec_final_group(v.msrc, mlen, body_end, v.mout, D, fb, flags);
-  fence_proxy_async_smem();
-  __syncwarp();
-  copy_out(dp, 12u * nu, out, lane);
+  if (!DIRECT) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    copy_out(dp, 12u * nu, out, lane);
+  }
 }
 
 // ------------------------------------------------------ short messages
@@ -716,9 +925,10 @@ __host__ __device__ __forceinline__ uint32_t warp_smem_bytes(int decode, int64_t
 // tile's copy, and leaves it beside the stage.
 template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off, int64_t tile,
-                 uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
-                 uint32_t flags, int64_t small_max) {
+    k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off,
+                 const int64_t* __restrict__ weight_off, int64_t tile, uint32_t stages,
+                 int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
+                 int64_t small_max) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
@@ -740,16 +950,14 @@ __global__ void __launch_bounds__(NT)
   uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, tile, S);
   uint8_t* obase = wbase + S * in_b;  // decode: the output buffer
 
-  const int64_t total = __ldg(tile_off + nmsg);
-  const int64_t nw = (int64_t)gridDim.x * (NT / 32);
-  const int64_t per = (total + nw - 1) / nw;
-  const int64_t t_begin = ((int64_t)blockIdx.x * (NT / 32) + warp) * per;
-  const int64_t t_end = tmin<int64_t>(total, t_begin + per);
+  int64_t t_begin, t_end, j_begin;
+  warp_tile_range(tile_off, weight_off, nmsg, tile, (int64_t)blockIdx.x * (NT / 32) + warp,
+                  (int64_t)gridDim.x * (NT / 32), lane, t_begin, t_end, j_begin);
   Msgs ms = msgs;
   ms.prepare(nmsg);
   WalkState& walk = walks[warp];  // used by lane 0
   if (lane == 0 && t_begin < t_end) {  // the first tiles' copies go out first
-    walk.j = owner_of(tile_off, nmsg, t_begin);
+    walk.j = j_begin;
     walk_load(walk, ms, tile_off);
     for (uint32_t s = 0; s < S && t_begin + s < t_end; ++s) {
       meta[warp][s] = walk_view(walk, ms, tile_off, t_begin + s, tile, out_tile);
@@ -776,10 +984,10 @@ __global__ void __launch_bounds__(NT)
       // the previous tile's bulk store has finished reading the output buffer
       if (lane == 0 && t > t_begin) bulk_wait_read(0);
       __syncwarp();
-      decode_tile(v, in, obase, table,
+      decode_tile<false>(v, in, obase, table,
                   reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j, lane, flags);
     } else {
-      encode_tile(v, in, table, lane, flags);
+      encode_tile<false>(v, in, table, lane, flags);
       fence_proxy_async_smem();  // the stage's reads come before its next copy
       __syncwarp();
     }
@@ -804,6 +1012,49 @@ __global__ void __launch_bounds__(NT)
     }
   }
   if (DECODE && lane == 0) bulk_wait_all();
+}
+
+// The same persistent walk without staging: every lane keeps the walk in
+// registers (one warp-instruction each, as on one lane), and the tiles'
+// units move straight between global memory and registers, so a warp needs
+// no shared memory, barrier or copy engine, and a tile may be longer than a
+// stage could hold.
+template <int NT, int DECODE, class Msgs>
+__global__ void __launch_bounds__(NT)
+    k_batch_direct(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off,
+                   const int64_t* __restrict__ weight_off, int64_t tile,
+                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
+                   int64_t small_max) {
+  __shared__ uint8_t table[DECODE ? 256 : 64];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (DECODE) {
+    init_tables(nullptr, table, flags & kFlagUrl);
+  } else {
+    init_tables(table, nullptr, flags & kFlagUrl);
+  }
+  const int64_t out_tile = out_tile_bytes(DECODE, tile);
+  int64_t t_begin, t_end, j_begin;
+  warp_tile_range(tile_off, weight_off, nmsg, tile, (int64_t)blockIdx.x * (NT / 32) + warp,
+                  (int64_t)gridDim.x * (NT / 32), lane, t_begin, t_end, j_begin);
+  Msgs ms = msgs;
+  ms.prepare(nmsg);
+  if (small_max > 0)
+    code_short_messages<DECODE>(ms, nmsg, small_max, table, first_bad, outlen, flags);
+  if (t_begin >= t_end) return;
+  WalkState walk;
+  walk.j = j_begin;
+  walk_load(walk, ms, tile_off);
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    TileView v = walk_view(walk, ms, tile_off, t, tile, out_tile);
+    v.o = v.ia = v.ib = 0u;  // nothing staged
+    if (DECODE) {
+      decode_tile<true>(v, nullptr, nullptr, table,
+                        reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j, lane,
+                        flags);
+    } else {
+      encode_tile<true>(v, nullptr, table, lane, flags);
+    }
+  }
 }
 
 // Per-message status: first bad character wins, then the length rule, then
@@ -834,42 +1085,49 @@ __global__ void k_batch_decode_init(int64_t nmsg, int64_t* __restrict__ first_ba
 
 // ------------------------------------------------------------------ host
 size_t batch_smem_bytes(int decode, const BatchConfig& c) {
+  if (c.kernel == 2) return 0;  // unstaged tiles
   return (size_t)(c.threads / 32) * warp_smem_bytes(decode, c.tile, (uint32_t)c.stages);
 }
 
 size_t batch_scratch_bytes(int64_t nmsg) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  return (size_t)(nmsg + 1) * 8 + (size_t)std::max<int64_t>(nparts, 1) * 16;
+  return (size_t)(nmsg + 1) * 16 + (size_t)std::max<int64_t>(nparts, 1) * 24;
 }
 
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
-                          int64_t* tile_off, int64_t tile, void* scratch_parts,
+                          int64_t* tile_off, int64_t* weight_off, int64_t tile, void* scratch_parts,
                           int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
                           uint32_t flags, int64_t small_max) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  int64_t* part_out = static_cast<int64_t*>(scratch_parts);
-  int64_t* part_tiles = part_out + std::max<int64_t>(nparts, 1);
+  int64_t* parts = static_cast<int64_t*>(scratch_parts);
   if (nparts > 0) {
     k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
                                                                 small_max, out_off, tile_off,
-                                                                part_out, part_tiles);
-    k_scan_parts<<<1, kScanThreads, 0, stream>>>(part_out, part_tiles, nparts);
+                                                                weight_off, parts, nparts);
+    k_scan_parts<<<1, kScanThreads, 0, stream>>>(parts, nparts);
   }
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
-  k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, tile_off, part_out, part_tiles,
-                                                   first_bad, outlen);
+  k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, tile_off, weight_off, parts,
+                                                   nparts, first_bad, outlen);
   return cudaGetLastError();
 }
 
 namespace {
 template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
-                        int32_t* status, int64_t* first_bad, int64_t* outlen,
-                        const BatchConfig& cfg, const DeviceInfo* di, uint32_t flags,
-                        cudaStream_t stream, int64_t small_max) {
+                        const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+                        int64_t* outlen, const BatchConfig& cfg, const DeviceInfo* di,
+                        uint32_t flags, cudaStream_t stream, int64_t small_max) {
+  const bool direct = cfg.kernel == 2;
   const size_t smem = batch_smem_bytes(decode, cfg);
-  const void* kernel = decode ? reinterpret_cast<const void*>(k_batch_code<NT, 1, Msgs>)
-                              : reinterpret_cast<const void*>(k_batch_code<NT, 0, Msgs>);
+  const void* kernel;
+  if (direct) {
+    kernel = decode ? reinterpret_cast<const void*>(k_batch_direct<NT, 1, Msgs>)
+                    : reinterpret_cast<const void*>(k_batch_direct<NT, 0, Msgs>);
+  } else {
+    kernel = decode ? reinterpret_cast<const void*>(k_batch_code<NT, 1, Msgs>)
+                    : reinterpret_cast<const void*>(k_batch_code<NT, 0, Msgs>);
+  }
   int fit = 0;
   cudaError_t e = kernel_prepare(kernel, smem, NT, &fit);
   if (e != cudaSuccess) return e;
@@ -877,15 +1135,27 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const int bps = cfg.blocks_per_sm > 0 ? std::min(fit, cfg.blocks_per_sm) : fit;
   const int grid = di->sm_count * bps;
   const uint32_t stages = (uint32_t)cfg.stages;
-  if (!decode) {
-    k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                          nullptr, nullptr, flags, small_max);
-    return cudaGetLastError();
+  if (direct) {
+    if (decode) {
+      k_batch_direct<NT, 1, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, weight_off,
+                                                           cfg.tile, first_bad, outlen, flags,
+                                                           small_max);
+    } else {
+      k_batch_direct<NT, 0, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, weight_off,
+                                                           cfg.tile, nullptr, nullptr, flags,
+                                                           small_max);
+    }
+  } else if (decode) {
+    k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, weight_off,
+                                                          cfg.tile, stages, first_bad, outlen,
+                                                          flags, small_max);
+  } else {
+    k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, weight_off,
+                                                          cfg.tile, stages, nullptr, nullptr,
+                                                          flags, small_max);
   }
-  k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, cfg.tile, stages,
-                                                        first_bad, outlen, flags, small_max);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !decode) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
   k_batch_decode_finish<Msgs><<<(unsigned)blocks, 256, 0, stream>>>(msgs, nmsg, status, first_bad,
                                                                    outlen, flags);
@@ -894,51 +1164,52 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
 
 template <class Msgs>
 cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
-                            int32_t* status, int64_t* first_bad, int64_t* outlen,
-                            const BatchConfig& cfg, uint32_t flags, cudaStream_t stream,
-                            int64_t small_max = 0) {
+                            const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+                            int64_t* outlen, const BatchConfig& cfg, uint32_t flags,
+                            cudaStream_t stream, int64_t small_max = 0) {
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
     case 128:
-      return launch_work<128>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, small_max);
+      return launch_work<128>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
+                              cfg, di, flags, stream, small_max);
     case 512:
-      return launch_work<512>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, small_max);
+      return launch_work<512>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
+                              cfg, di, flags, stream, small_max);
     default:
-      return launch_work<256>(decode, msgs, nmsg, tile_off, status, first_bad, outlen, cfg, di,
-                              flags, stream, small_max);
+      return launch_work<256>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
+                              cfg, di, flags, stream, small_max);
   }
 }
 }  // namespace
 
 cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
-                              const int64_t* tile_off, int32_t* status, int64_t* first_bad,
-                              int64_t* outlen, const BatchConfig& cfg, bool init_results,
-                              cudaStream_t stream, uint32_t flags) {
+                              const int64_t* tile_off, const int64_t* weight_off,
+                              int32_t* status, int64_t* first_bad, int64_t* outlen,
+                              const BatchConfig& cfg, bool init_results, cudaStream_t stream,
+                              uint32_t flags) {
   if (decode && init_results) {
     const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
     k_batch_decode_init<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, first_bad, outlen);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, tile_off, status, first_bad, outlen,
-                         cfg, flags, stream);
+  return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, tile_off, weight_off, status,
+                         first_bad, outlen, cfg, flags, stream);
 }
 
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
-  const int64_t small_max = cfg.kernel == 0 ? batch_small_max(a.decode) : 0;
-  cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, cfg.tile,
-                                a.parts, a.decode ? a.first_bad : nullptr,
+  const int64_t small_max = cfg.kernel != 1 ? batch_small_max(a.decode) : 0;
+  cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, a.weight_off,
+                                cfg.tile, a.parts, a.decode ? a.first_bad : nullptr,
                                 a.decode ? a.outlen : nullptr, a.stream, a.flags, small_max);
   if (e != cudaSuccess) return e;
   // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
   PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
   // short messages go one thread each at the start of the tile kernel
-  return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.status, a.first_bad, a.outlen, cfg,
-                         a.flags, a.stream, small_max);
+  return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.weight_off, a.status, a.first_bad,
+                         a.outlen, cfg, a.flags, a.stream, small_max);
 }
 
 // Longest messages (input bytes / characters) coded one thread each by

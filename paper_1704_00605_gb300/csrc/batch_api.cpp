@@ -12,18 +12,22 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
   if (c.threads != 128 && c.threads != 256 && c.threads != 512) return false;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) return false;
   if (c.stages < 2 || c.stages > 6) return false;
-  if (c.kernel < 0 || c.kernel > 1) return false;
+  if (c.kernel < 0 || c.kernel > 2) return false;
   const int64_t row = decode ? 512 : 384;  // one unit per lane of a warp
-  if (c.tile < row || c.tile > 16 * row || c.tile % row) return false;
+  const int64_t max_rows = c.kernel == 2 ? 64 : 16;  // unstaged tiles need no shared memory
+  if (c.tile < row || c.tile > max_rows * row || c.tile % row) return false;
   return batch_smem_bytes(decode, c) <= kBatchSmemLimit;
 }
 
-// Shapes measured fastest on GB300 with the tuner: mean message length
-// below 1 KiB (262,144 messages of 256 B) and above (100,000 messages of
-// 6.3 KiB on average, and 256 of 1 MiB). mean_len < 0: unknown.
+// Shapes measured fastest on GB300: mean message length below 1 KiB
+// (262,144 messages of 256 B) and above (100,000 messages of 6.3 KiB on
+// average, and 64 of 1 MiB). Decoding longer messages, unstaged tiles of 32
+// rows beat staged ones (a shared-memory output buffer and its bulk store
+// per tile, and tiles limited to 8 rows); encoding, the two are even and
+// staged tiles stay. mean_len < 0: unknown.
 BatchConfig default_batch_config(int decode, int64_t mean_len) {
   const bool small = mean_len >= 0 && mean_len < 1024;
-  if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 4096, 0, 2};
+  if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 16384, 0, 2, 2};
   return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2};
 }
 
@@ -59,7 +63,7 @@ int run_batch(BatchArgs a) {
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(a.nmsg), a.stream);
   if (e != cudaSuccess) return cuda_status(e, "batch: scratch");
-  batch_scratch_split(scratch, a.nmsg, &a.tile_off, &a.parts);
+  batch_scratch_split(scratch, a.nmsg, &a.tile_off, &a.weight_off, &a.parts);
   const BatchConfig cfg = tuned_batch_config(a.decode, a.nmsg);
   e = batch_launch(a, cfg);
   cudaError_t ef = cudaFreeAsync(scratch, a.stream);
@@ -85,11 +89,11 @@ int b64_batch_out_offsets_ex(int decode, const int64_t* in_off, int64_t nmsg, in
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(nmsg), s);
   if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets: scratch");
-  int64_t* tile_off;
+  int64_t *tile_off, *weight_off;
   void* parts;
-  batch_scratch_split(scratch, nmsg, &tile_off, &parts);
-  e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, tile_off, 1 << 20, parts, nullptr,
-                    nullptr, s, (uint32_t)flags);
+  batch_scratch_split(scratch, nmsg, &tile_off, &weight_off, &parts);
+  e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, tile_off, weight_off, 1 << 20, parts,
+                    nullptr, nullptr, s, (uint32_t)flags);
   cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e == cudaSuccess) e = ef;
   if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets");

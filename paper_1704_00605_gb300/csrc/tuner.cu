@@ -146,10 +146,15 @@ std::vector<b64_shape> batch_candidates(int decode) {
   const int64_t row = decode ? 512 : 384;
   for (int threads : {128, 256})
     for (int rows : {2, 4, 8, 12, 16})
-      for (int stages : {2, 3, 4, 6}) {
+      for (int stages : {2, 3, 4, 6}) {  // staged tiles (kernel choice 0)
         const b64_shape s{threads, 0, stages, 0, row * rows, 0.f};
         if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
       }
+  for (int threads : {128, 256})
+    for (int rows : {8, 16, 32, 64}) {  // unstaged tiles (kernel choice 2)
+      const b64_shape s{threads, 2, 2, 0, row * rows, 0.f};
+      if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
+    }
   return out;
 }
 
@@ -342,7 +347,7 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
   ba.status = st;
   ba.first_bad = fb;
   ba.outlen = ol;
-  if (batch) batch_scratch_split(scratch, nmsg, &ba.tile_off, &ba.parts);
+  if (batch) batch_scratch_split(scratch, nmsg, &ba.tile_off, &ba.weight_off, &ba.parts);
   if (decode) {  // decode input = encoding of the random bytes
     if (batch) {
       BatchArgs ea = ba;

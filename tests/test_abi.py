@@ -133,6 +133,17 @@ def test_shape_table_host_side(g, tmp_path):
         g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=512, tile=8192, stages=4)
     with pytest.raises(g.Gb64Error):
         g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=128, tile=1536, stages=7)
+    # unstaged tiles (kernel choice 2) use no shared memory: up to 64 rows
+    g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=512, tile=64 * 512, stages=2,
+                    units_per_thread=2)
+    with pytest.raises(g.Gb64Error):
+        g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=128, tile=65 * 512,
+                        units_per_thread=2)
+    with pytest.raises(g.Gb64Error):  # staged tiles: at most 16 rows
+        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=128, tile=17 * 384,
+                        units_per_thread=0)
+    with pytest.raises(g.Gb64Error):
+        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, units_per_thread=3)
     g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=512, tile=1024, stages=2,
                     blocks_per_sm=4)
     assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["stages"] == 2

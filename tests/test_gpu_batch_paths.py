@@ -1,8 +1,8 @@
 """The kernels of the batched codec against the oracle (exact), on the same
-batches: the default (short messages one thread each, the per-warp tile
-kernels for the rest) and the per-warp tile kernels for every message,
-chosen through the shape table's kernel choice (0, 1), each with buffers on
-and off a 16-byte boundary. Batches mix empty, tiny and large messages, lengths of
+batches: short messages one thread each with staged per-warp tiles for the
+rest, staged tiles for every message, and short messages with unstaged
+tiles (of 8 and of 64 rows), chosen through the shape table's kernel choice
+(0, 1, 2), each with buffers on and off a 16-byte boundary. Batches mix empty, tiny and large messages, lengths of
 every class mod 3 and mod 4, messages that straddle tiles and tiles that
 hold hundreds of messages, padding, errors at every kind of position, and
 the decode flags."""
@@ -16,18 +16,23 @@ from paper_1704_00605_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 URL, NOPAD, STRICT = 1, 2, 4
-DEFAULT, PER_WARP = 0, 1
+# kernel choice, and tile rows of encode and decode
+STAGED, STAGED_ALL, DIRECT, DIRECT_LONG = (0, 16, 8), (1, 16, 8), (2, 8, 8), (2, 64, 64)
+MODES = (STAGED, STAGED_ALL, DIRECT, DIRECT_LONG)
 
 
 @contextlib.contextmanager
 def kernel_choice(gb64, mode):
     """Batch calls (whose total size the library does not know) use the
-    given kernel choice while the block runs."""
+    given kernel choice and tile rows while the block runs."""
+    kernel, enc_rows, dec_rows = mode
     kinds = (gb64.B64_KIND_ENCODE_BATCH, gb64.B64_KIND_DECODE_BATCH)
     saved = [gb64.b64_shape_get(k, -1, 1) for k in kinds]
     try:
         for k in kinds:
-            gb64.b64_shape_set(k, -1, 1, units_per_thread=mode)
+            dec = k == gb64.B64_KIND_DECODE_BATCH
+            gb64.b64_shape_set(k, -1, 1, units_per_thread=kernel, threads=128, stages=2,
+                               tile=dec_rows * 512 if dec else enc_rows * 384)
         yield
     finally:
         for k, sh in zip(kinds, saved):
@@ -113,7 +118,7 @@ def test_encode_both_paths(gb64, oracle, seed):
     exp, exp_off = oracle.encode_batch(data, off)
     exp_url = np.concatenate([oracle.encode_ex(data[off[j]:off[j + 1]], URL)
                               for j in range(off.size - 1)])
-    for mode in (DEFAULT, PER_WARP):
+    for mode in MODES:
         with kernel_choice(gb64, mode):
             for shift in (0, 4, 8, 12, 1):  # outputs on and off a 16-byte boundary
                 out, out_off = _encode(gb64, data, off, shift)
@@ -142,7 +147,7 @@ def test_decode_both_paths_valid_and_errors(gb64, oracle, seed):
             chars[p] = NON_ALPHABET_NON_PAD[int(rng.integers(0, NON_ALPHABET_NON_PAD.size))]
             nbad += 1
     assert nbad > 10
-    for mode in (DEFAULT, PER_WARP):
+    for mode in MODES:
         with kernel_choice(gb64, mode):
             for shift in (0, 3, 8):  # inputs on and off a 16-byte boundary
                 _check_decode(oracle, chars, coff, _decode(gb64, chars, coff, shift), 0)
@@ -168,7 +173,7 @@ def test_decode_both_paths_lengths_not_multiple_of_4(gb64, oracle, flags):
             chars[b - 1] = 0x3D
         elif b > a and r < 0.4:
             chars[int(rng.integers(a, b))] = int(rng.integers(0, 256))
-    for mode in (DEFAULT, PER_WARP):
+    for mode in MODES:
         with kernel_choice(gb64, mode):
             for shift in (0, 5):
                 _check_decode(oracle, chars, off, _decode(gb64, chars, off, shift, flags), flags)
@@ -233,6 +238,6 @@ def test_lengths_around_the_short_message_limit(gb64, oracle, flags):
             chars[j][int(rng.integers(0, chars[j].size))] = NON_ALPHABET_NON_PAD[int(rng.integers(0, 191))]
     coff = W.offsets_from_lengths(np.array([c.size for c in chars], dtype=np.int64))
     allc = np.concatenate(chars)
-    for mode in (DEFAULT, PER_WARP):
+    for mode in MODES:
         with kernel_choice(gb64, mode):
             _check_decode(oracle, allc, coff, _decode(gb64, allc, coff, 0, flags), flags)

@@ -68,15 +68,19 @@ def test_tune_batch_and_every_candidate_is_exact(gb64, oracle, restore_shapes, k
     assert len(trials) >= 10 and all(t["ms"] > 0 for t in trials)
     exp_enc, exp_off = oracle.encode_batch(data, off)
     src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
-    for t in trials:
-        shape = dict(threads=t["threads"], tile=t["tile"], blocks_per_sm=t["blocks_per_sm"],
-                     stages=t["stages"], units_per_thread=t["units_per_thread"])
-        if kind == 2:
-            gb64.b64_shape_set(2, total, nmsg, **shape)
-        else:
-            gb64.b64_shape_set(3, int(exp_off[-1]), nmsg, **shape)
-        enc, eoff = gb64.b64_encode_batch(src, doff)
-        assert np.array_equal(enc.cpu().numpy()[:exp_enc.size], exp_enc)
-        dst, out_off, st, fb, ol = gb64.b64_decode_batch(enc, eoff)
-        assert int((st != 0).sum()) == 0
-        assert torch.equal(ol.cpu(), torch.from_numpy(np.diff(off)))
+    # packed batch calls (offsets on the device: mean length unknown to the
+    # host) take the shape of the unknown-size bucket: force it there
+    fields = ("threads", "units_per_thread", "stages", "blocks_per_sm", "tile")
+    saved = gb64.b64_shape_get(kind, -1, 1)
+    try:
+        for t in trials:
+            gb64.b64_shape_set(kind, -1, 1, **{f: t[f] for f in fields})
+            enc, eoff = gb64.b64_encode_batch(src, doff)
+            assert np.array_equal(enc.cpu().numpy()[:exp_enc.size], exp_enc), t
+            dst, out_off, st, fb, ol = gb64.b64_decode_batch(enc, eoff)
+            assert int((st != 0).sum()) == 0, t
+            assert torch.equal(ol.cpu(), torch.from_numpy(np.diff(off))), t
+            assert all(np.array_equal(dst[out_off[j]:out_off[j] + ol[j]].cpu().numpy(),
+                                      data[off[j]:off[j + 1]]) for j in range(0, nmsg, 97)), t
+    finally:
+        gb64.b64_shape_set(kind, -1, 1, **{f: saved[f] for f in fields})
