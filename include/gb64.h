@@ -125,7 +125,7 @@ int b64_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg, uint8
  * the call (a fixed memory budget or an allocator owned by someone else, or
  * a hot path that cannot afford cudaMalloc/cudaFree synchronizing the
  * device). Same arguments, kernels and results as b64_decode_batch, but the
- * scratch lives in a fixed array inside the library (about 1 MiB per GPU
+ * scratch lives in a fixed array inside the library (about 576 KiB per GPU
  * that uses it, held until the process exits) instead of coming from the
  * stream-ordered allocator. At most 65536 messages per call; a larger nmsg
  * returns B64_ERR_ARG with nothing enqueued. Every call on a device shares

@@ -2,16 +2,20 @@
 // direction.
 //
 //   1. k_scan_local / k_scan_parts / k_scan_add: a device prefix sum over the
-//      messages of (output length, tile count). Output length is
-//      4 * ceil(n / 3) (encode) or 3 * floor(m / 4) (decode capacity); the
-//      tile count is ceil(length / tile). The exclusive sums become out_off
-//      (returned to the caller) and tile_off (scratch).
-//   2. k_batch_code (encode or decode): a persistent grid in which every
-//      warp owns a contiguous range of the T tiles, finds the owning message
-//      of its first tile by binary search in tile_off and advances through
-//      the following messages by a forward scan. Tiles reach shared memory
-//      by bulk copies (TMA) several tiles ahead and are coded with the unit
-//      codecs of common.cuh; outputs leave by bulk stores. Per-message
+//      messages of (output length, weight). Output length is
+//      4 * ceil(n / 3) (encode) or 3 * floor(m / 4) (decode capacity); a
+//      message longer than the short-message limit is cut into
+//      ceil(length / tile) tiles and weighs its length plus a fixed cost per
+//      tile, a shorter one weighs 0. The exclusive sums become out_off
+//      (returned to the caller) and weight_off (scratch).
+//   2. k_batch_code / k_batch_direct (encode or decode): a persistent grid.
+//      Its threads first code the short messages one each; then every warp
+//      takes the tiles that start in its equal share of the total weight,
+//      finds the message of its first one by a search in weight_off and
+//      walks forward message by message. k_batch_code stages each tile in
+//      shared memory by a bulk copy (TMA) several tiles ahead; k_batch_direct
+//      reads and writes the tiles' units straight from and to global
+//      memory. Both code units with the codecs of common.cuh; per-message
 //      padding (encode) and final quad, error index and length rule
 //      (decode) are handled in the tile that holds the message end.
 //   3. k_batch_decode_finish: per-message status, first_bad and outlen.
@@ -35,166 +39,178 @@ constexpr int64_t kNoBad = INT64_MAX;
 constexpr int64_t kTileCost = kBatchTileCost;
 
 // ----------------------------------------------------------------- scan
-// Output length, tile count and weight of one message; messages of at most
-// small_max bytes get no tiles (threads code them one each) and no weight.
-// A message's weight, its length plus kTileCost per tile, is what the
-// tile kernels divide evenly among their warps.
+// floor(n / d) for 0 <= n < 2^48 and 2 <= d < 2^16 by one multiply-high:
+// with m = ceil(2^64 / d) = d^-1 * (2^64 + e), 0 <= e < d, n * m / 2^64 =
+// n / d + n * e / (d * 2^64) exceeds n / d by less than 1 / d, too little
+// to reach the next integer. Saves the 64-bit division routine (and its
+// registers) in the tile walk; device buffers are far below 2^48 bytes.
+struct DivBy {
+  uint64_t m;
+  __host__ __device__ static DivBy of(int64_t d) { return DivBy{~0ull / (uint64_t)d + 1}; }
+  __device__ __forceinline__ int64_t operator()(int64_t n) const {
+    return (int64_t)__umul64hi((uint64_t)n, m);
+  }
+};
+
+// Tiles of a message of len bytes / characters: none at most small_max
+// (threads code it one each), else ceil(len / tile). The scan and the tile
+// walk both count them this way.
+__device__ __forceinline__ int64_t msg_tiles(int64_t len, int64_t tile, DivBy by_tile,
+                                             int64_t small_max) {
+  return len > small_max ? by_tile(len + tile - 1) : 0;
+}
+
+// Weight of a message with `tiles` tiles: what the tile kernels divide
+// evenly among their warps.
+__device__ __forceinline__ int64_t msg_weight(int64_t len, int64_t tiles) {
+  return tiles ? len + tiles * kTileCost : 0;
+}
+
+// Output length and weight of one message.
 __device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, uint32_t flags,
-                                           int64_t small_max, int64_t& outv, int64_t& tiles,
-                                           int64_t& weight) {
+                                           int64_t small_max, int64_t& outv, int64_t& weight) {
   if (len < 0) len = 0;
   outv = decode ? (int64_t)decoded_cap_flags((uint64_t)len, flags)
                 : (int64_t)encoded_len_flags((uint64_t)len, flags);
-  tiles = len > small_max ? (len + tile - 1) / tile : 0;
-  weight = tiles ? len + tiles * kTileCost : 0;
+  weight = msg_weight(len, msg_tiles(len, tile, DivBy::of(tile), small_max));
 }
 
-// Three int64 running sums (output, tiles, weight).
-struct Sum3 {
-  int64_t v[3];
-};
-
-__device__ __forceinline__ Sum3 shfl_up3(const Sum3& x, int d) {
-  Sum3 r;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) r.v[i] = __shfl_up_sync(0xFFFFFFFFu, x.v[i], d);
-  return r;
-}
-
-// Block-wide exclusive scan of x; tot receives the block total.
-__device__ __forceinline__ void block_exclusive_scan3(Sum3& x, Sum3& tot) {
-  __shared__ int64_t ws[3][kScanThreads / 32];
+// Block-wide exclusive scan of a pair of int64 values; returns the block total.
+__device__ __forceinline__ void block_exclusive_scan2(int64_t& a, int64_t& b, int64_t& tot_a,
+                                                      int64_t& tot_b) {
+  __shared__ int64_t wa[kScanThreads / 32], wb[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Sum3 inc = x;  // inclusive within the warp
+  int64_t ia = a, ib = b;  // inclusive within the warp
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const Sum3 y = shfl_up3(inc, d);
-    if (lane >= d)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) inc.v[i] += y.v[i];
+    const int64_t xa = __shfl_up_sync(0xFFFFFFFFu, ia, d);
+    const int64_t xb = __shfl_up_sync(0xFFFFFFFFu, ib, d);
+    if (lane >= d) {
+      ia += xa;
+      ib += xb;
+    }
   }
-  if (lane == 31)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ws[i][warp] = inc.v[i];
+  if (lane == 31) {
+    wa[warp] = ia;
+    wb[warp] = ib;
+  }
   __syncthreads();
   if (warp == 0) {
-    Sum3 w;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) w.v[i] = lane < kScanThreads / 32 ? ws[i][lane] : 0;
+    int64_t sa = lane < kScanThreads / 32 ? wa[lane] : 0;
+    int64_t sb = lane < kScanThreads / 32 ? wb[lane] : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const Sum3 y = shfl_up3(w, d);
-      if (lane >= d)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w.v[i] += y.v[i];
+      const int64_t xa = __shfl_up_sync(0xFFFFFFFFu, sa, d);
+      const int64_t xb = __shfl_up_sync(0xFFFFFFFFu, sb, d);
+      if (lane >= d) {
+        sa += xa;
+        sb += xb;
+      }
     }
-    if (lane < kScanThreads / 32)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) ws[i][lane] = w.v[i];  // inclusive over warps
+    if (lane < kScanThreads / 32) {
+      wa[lane] = sa;  // inclusive over warps
+      wb[lane] = sb;
+    }
   }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int64_t before = warp ? ws[i][warp - 1] : 0;
-    tot.v[i] = ws[i][kScanThreads / 32 - 1];
-    x.v[i] = before + inc.v[i] - x.v[i];
-  }
+  const int64_t pa = warp ? wa[warp - 1] : 0, pb = warp ? wb[warp - 1] : 0;
+  tot_a = wa[kScanThreads / 32 - 1];
+  tot_b = wb[kScanThreads / 32 - 1];
+  a = pa + ia - a;
+  b = pb + ib - b;
 }
 
-// The block totals: parts[i * nparts + p] for sum i of block p.
 __global__ void __launch_bounds__(kScanThreads)
     k_scan_local(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
                  uint32_t flags, int64_t small_max, int64_t* __restrict__ out_off,
-                 int64_t* __restrict__ tile_off, int64_t* __restrict__ weight_off,
-                 int64_t* __restrict__ parts, int64_t nparts) {
+                 int64_t* __restrict__ weight_off, int64_t* __restrict__ part_out,
+                 int64_t* __restrict__ part_weight) {
   const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
-  Sum3 item[kScanItems];
-  Sum3 sum = {{0, 0, 0}};
+  int64_t vo[kScanItems], vw[kScanItems];
+  int64_t so = 0, sw = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const int64_t j = base + k;
-    item[k] = Sum3{{0, 0, 0}};
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t j = base + i;
+    vo[i] = vw[i] = 0;
     if (j < nmsg)
-      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, item[k].v[0],
-                 item[k].v[1], item[k].v[2]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) sum.v[i] += item[k].v[i];
+      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, vo[i], vw[i]);
+    so += vo[i];
+    sw += vw[i];
   }
-  Sum3 tot;
-  block_exclusive_scan3(sum, tot);
+  int64_t eo = so, ew = sw, to, tw;
+  block_exclusive_scan2(eo, ew, to, tw);
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const int64_t j = base + k;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) sum.v[i] += item[k].v[i];
-    if (j < nmsg) {  // inclusive within the block; k_scan_add adds the block base
-      out_off[j + 1] = sum.v[0];
-      tile_off[j + 1] = sum.v[1];
-      weight_off[j + 1] = sum.v[2];
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t j = base + i;
+    eo += vo[i];
+    ew += vw[i];
+    if (j < nmsg) {
+      out_off[j + 1] = eo;  // inclusive within the block; k_scan_add adds the block base
+      weight_off[j + 1] = ew;
     }
   }
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) parts[i * nparts + blockIdx.x] = tot.v[i];
+  if (threadIdx.x == 0) {
+    part_out[blockIdx.x] = to;
+    part_weight[blockIdx.x] = tw;
+  }
 }
 
 // One CTA: exclusive scan of the block totals, in place.
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_parts(int64_t* __restrict__ parts, int64_t nparts) {
-  __shared__ int64_t carry[3];
-  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    k_scan_parts(int64_t* __restrict__ part_out, int64_t* __restrict__ part_weight,
+                 int64_t nparts) {
+  __shared__ int64_t carry_o, carry_w;
+  if (threadIdx.x == 0) carry_o = carry_w = 0;
   __syncthreads();
   for (int64_t c = 0; c < nparts; c += kScanThreads) {
-    const int64_t p = c + threadIdx.x;
-    Sum3 x;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x.v[i] = p < nparts ? parts[i * nparts + p] : 0;
-    Sum3 tot;
-    block_exclusive_scan3(x, tot);
-    if (p < nparts)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) parts[i * nparts + p] = x.v[i] + carry[i];
+    const int64_t i = c + threadIdx.x;
+    int64_t a = i < nparts ? part_out[i] : 0, b = i < nparts ? part_weight[i] : 0;
+    int64_t ta, tb;
+    block_exclusive_scan2(a, b, ta, tb);
+    if (i < nparts) {
+      part_out[i] = a + carry_o;
+      part_weight[i] = b + carry_w;
+    }
     __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) carry[i] += tot.v[i];
+    if (threadIdx.x == 0) {
+      carry_o += ta;
+      carry_w += tb;
+    }
     __syncthreads();
   }
 }
 
 __global__ void k_scan_add(int64_t nmsg, int64_t* __restrict__ out_off,
-                           int64_t* __restrict__ tile_off, int64_t* __restrict__ weight_off,
-                           const int64_t* __restrict__ parts, int64_t nparts,
-                           int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
+                           int64_t* __restrict__ weight_off, const int64_t* __restrict__ part_out,
+                           const int64_t* __restrict__ part_weight, int64_t* __restrict__ first_bad,
+                           int64_t* __restrict__ outlen) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) {
     out_off[0] = 0;
-    tile_off[0] = 0;
     weight_off[0] = 0;
   }
   if (j >= nmsg) return;
   const int64_t p = j / kScanPerBlock;
-  out_off[j + 1] += parts[p];
-  tile_off[j + 1] += parts[nparts + p];
-  weight_off[j + 1] += parts[2 * nparts + p];
+  out_off[j + 1] += part_out[p];
+  weight_off[j + 1] += part_weight[p];
   if (first_bad) first_bad[j] = kNoBad;
   if (outlen) outlen[j] = 0;
 }
 
 // ------------------------------------------------------------ tile walk
-// Largest j in [0, nmsg) with tile_off[j] <= t (tile_off non-decreasing,
-// t < tile_off[nmsg]). The whole warp searches: each round its 32 lanes
-// probe 32 evenly spaced offsets and the count of those <= t narrows the
-// interval 33-fold (4 dependent loads for 10^5 messages, not 17).
-__device__ __forceinline__ int64_t owner_of_warp(const int64_t* tile_off, int64_t nmsg, int64_t t,
+// Largest j in [0, nmsg) with off[j] <= x (off non-decreasing, off[0] <= x
+// < off[nmsg]). The whole warp searches: each round its 32 lanes probe 32
+// evenly spaced offsets and the count of those <= x narrows the interval
+// 33-fold (4 dependent loads for 10^5 messages, not 17).
+__device__ __forceinline__ int64_t owner_of_warp(const int64_t* off, int64_t nmsg, int64_t x,
                                                  uint32_t lane) {
-  int64_t lo = 0, hi = nmsg;  // invariant: tile_off[lo] <= t < tile_off[hi]
+  int64_t lo = 0, hi = nmsg;  // invariant: off[lo] <= x < off[hi]
   while (hi - lo > 1) {
     const int64_t span = hi - lo;
     // probes lo < p_0 <= p_1 <= ... <= p_31 < hi
     const int64_t p = lo + 1 + (span - 1) * (int64_t)lane / 32;
-    const uint32_t le = __ballot_sync(0xFFFFFFFFu, __ldg(tile_off + p) <= t);
-    const int c = __popc(le);  // the probes <= t are lanes [0, c)
+    const uint32_t le = __ballot_sync(0xFFFFFFFFu, __ldg(off + p) <= x);
+    const int c = __popc(le);  // the probes <= x are lanes [0, c)
     const int64_t below = __shfl_sync(0xFFFFFFFFu, p, c > 0 ? c - 1 : 0);
     const int64_t above = __shfl_sync(0xFFFFFFFFu, p, c < 32 ? c : 31);
     if (c > 0) lo = below;
@@ -203,69 +219,12 @@ __device__ __forceinline__ int64_t owner_of_warp(const int64_t* tile_off, int64_
   return lo;
 }
 
-// The same search for two targets at once: lanes 0-15 find the owner of
-// their x, lanes 16-31 of theirs (16 probes a round each).
-__device__ __forceinline__ int64_t owner_of_halves(const int64_t* off, int64_t nmsg, int64_t x,
-                                                   uint32_t lane) {
-  const uint32_t h = lane >> 4, k = lane & 15u;
-  int64_t lo = 0, hi = nmsg;  // invariant: off[lo] <= x < off[hi]
-  while (__any_sync(0xFFFFFFFFu, hi - lo > 1)) {
-    const int64_t span = hi - lo;
-    // probes lo < p_0 <= ... <= p_15 < hi (p = hi <= nmsg once span is 1)
-    const int64_t p = lo + 1 + (span - 1) * (int64_t)k / 16;
-    const uint32_t le = __ballot_sync(0xFFFFFFFFu, __ldg(off + p) <= x);
-    const int c = __popc((le >> (16u * h)) & 0xFFFFu);
-    const int64_t below = __shfl_sync(0xFFFFFFFFu, p, (int)(16u * h) + (c > 0 ? c - 1 : 0));
-    const int64_t above = __shfl_sync(0xFFFFFFFFu, p, (int)(16u * h) + (c < 16 ? c : 15));
-    if (span > 1) {
-      if (c > 0) lo = below;
-      if (c < 16) hi = above;
-    }
-  }
-  return lo;
-}
-
-// The tiles [t_begin, t_end) of warp w of the grid's nw warps. With weight
-// offsets the warps split the total weight evenly, a warp taking the tiles
-// that start (tile k of message j starts at weight_off[j] + k * (tile +
-// kTileCost)) in its share: tiles of one message are equal but the last, and
-// messages differ, so equal tile counts would not be equal work. Without
-// them (host-built descriptor batches) every warp gets the same count.
-// j_begin: a message at or before the one holding t_begin (the walk moves
-// forward from it), when t_begin < t_end.
-__device__ __forceinline__ void warp_tile_range(const int64_t* tile_off, const int64_t* weight_off,
-                                                int64_t nmsg, int64_t tile, int64_t w, int64_t nw,
-                                                uint32_t lane, int64_t& t_begin, int64_t& t_end,
-                                                int64_t& j_begin) {
-  const int64_t total = __ldg(tile_off + nmsg);
-  if (!weight_off || total == 0) {
-    const int64_t per = (total + nw - 1) / nw;
-    t_begin = tmin<int64_t>(total, w * per);
-    t_end = tmin<int64_t>(total, t_begin + per);
-    j_begin = t_begin < t_end ? owner_of_warp(tile_off, nmsg, t_begin, lane) : 0;
-    return;
-  }
-  const int64_t wt = __ldg(weight_off + nmsg);  // > 0 when there are tiles
-  const bool last = w + 1 == nw;
-  // lanes 0-15: the start of the share, 16-31: its end (the next share's start)
-  const int64_t x = lane < 16 ? wt * w / nw : (last ? 0 : wt * (w + 1) / nw);
-  const int64_t j = owner_of_halves(weight_off, nmsg, x, lane);
-  const int64_t t0 = __ldg(tile_off + j), nt = __ldg(tile_off + j + 1) - t0;
-  const int64_t k = (x - __ldg(weight_off + j) + tile + kTileCost - 1) / (tile + kTileCost);
-  const int64_t t = t0 + tmin<int64_t>(k, nt);  // the first tile starting at or after x
-  t_begin = __shfl_sync(0xFFFFFFFFu, t, 0);
-  t_end = last ? total : __shfl_sync(0xFFFFFFFFu, t, 16);
-  j_begin = __shfl_sync(0xFFFFFFFFu, j, 0);  // t_begin is in j or a later message
-}
-
-// One message as a tile sees it: its bytes, its output, and the bounds that
-// aligned-word reads near its ends must stay within.
+// One message as a tile sees it: its bytes and its output. Aligned-word
+// reads near its ends stay within the bounds its batch gives (lo, hi).
 struct Msg {
   const uint8_t* src;
   int64_t len;
   uint8_t* out;
-  const uint8_t* lo;
-  const uint8_t* hi;
 };
 
 // Messages packed back to back in one buffer (the batched C ABI).
@@ -277,8 +236,11 @@ struct PackedMsgs {
   const uint8_t* src_hi;
   __device__ __forceinline__ Msg get(int64_t j) const {
     const int64_t m0 = __ldg(in_off + j);
-    return Msg{src + m0, __ldg(in_off + j + 1) - m0, dst + __ldg(out_off + j), src, src_hi};
+    return Msg{src + m0, __ldg(in_off + j + 1) - m0, dst + __ldg(out_off + j)};
   }
+  // the packed input buffer
+  __device__ __forceinline__ const uint8_t* lo(const Msg&) const { return src; }
+  __device__ __forceinline__ const uint8_t* hi(const Msg&) const { return src_hi; }
   __device__ __forceinline__ int64_t len(int64_t j) const {
     return __ldg(in_off + j + 1) - __ldg(in_off + j);
   }
@@ -291,15 +253,18 @@ struct DescMsgs {
   uint8_t* dst;
   __device__ __forceinline__ Msg get(int64_t j) const {
     const MsgDesc d = desc[j];
-    return Msg{d.src, d.len, dst + d.out_off, d.src, d.src + d.len};
+    return Msg{d.src, d.len, dst + d.out_off};
   }
+  // the message itself
+  __device__ __forceinline__ const uint8_t* lo(const Msg& m) const { return m.src; }
+  __device__ __forceinline__ const uint8_t* hi(const Msg& m) const { return m.src + m.len; }
   __device__ __forceinline__ int64_t len(int64_t j) const { return desc[j].len; }
   __device__ __forceinline__ void prepare(int64_t) {}
 };
 
 // ------------------------------------------------------ warp pipeline
-// Every warp walks its own contiguous range of tiles. Tile t of message j
-// holds input bytes [t0, t0 + len) of j (len <= tile). The tile's
+// Every warp walks its own range of tiles (see WalkState below). Tile k of
+// message j holds input bytes [t0, t0 + len) of j, t0 = k * tile, len <= tile. The tile's
 // 16-byte-aligned interior is copied into the warp's input stage by one bulk
 // copy, issued `stages` tiles ahead; stage position o + i holds input byte
 // t0 + i, o being the tile start's address mod 16, so positions [ia, ib)
@@ -322,41 +287,71 @@ struct TileView {
   uint32_t ia, ib;
 };
 
-// The issuing lane's walk over its tiles: the current message is kept in
-// the warp's slot of shared memory (not in registers, which every lane would
-// pay for), so the offsets arrays are read only when the walk enters the
-// next message (tile_off is non-decreasing; tiles are visited in order).
-struct WalkState {
-  Msg m;
-  int64_t j;        // current message
-  int64_t t_first;  // its first tile
-  int64_t t_end;    // one past its last tile
+// A warp's walk over its tiles. Warp w of the grid's nw warps owns the
+// weight [W*w/nw, W*(w+1)/nw) of the batch's total W and takes the tiles
+// that start in it, tile k of message j starting at weight weight_off[j] +
+// k * (tile + kTileCost): equal shares of bytes and tiles, whatever the mix
+// of lengths (equal tile counts would not be equal work, the last tile of
+// a message being short). The walk finds the message of its first tile by
+// a search, then moves forward one message at a time, counting each one's
+// tiles from its length as the scan did; the offsets arrays are read only
+// when it enters the next message.
+// The tile geometry of a launch.
+struct TileShape {
+  int64_t tile;       // input bytes / characters of a whole tile
+  int64_t out_tile;   // its output bytes
+  int64_t small_max;  // longest message coded one thread each (0: none)
+  DivBy by_tile;      // division by tile
+  DivBy by_step;      // division by tile + kTileCost
 };
 
+struct WalkState {
+  Msg m;
+  int64_t j;       // current message
+  int64_t ntiles;  // its tiles
+  int64_t k;       // its next tile
+  int64_t wk;      // weight offset of tile k
+  int64_t w_end;   // end of the warp's share
+};
+
+// Starts a walk at message j (found by owner_of_warp for w_begin), at its
+// first tile starting at or after w_begin.
 template <class Msgs>
-__device__ __forceinline__ void walk_load(WalkState& w, const Msgs& ms, const int64_t* tile_off) {
-  w.m = ms.get(w.j);
-  w.t_first = __ldg(tile_off + w.j);
-  w.t_end = __ldg(tile_off + w.j + 1);
+__device__ __forceinline__ void walk_begin(WalkState& w, const Msgs& ms, const int64_t* weight_off,
+                                           int64_t j, int64_t w_begin, int64_t w_end,
+                                           const TileShape& ts) {
+  w.j = j;
+  w.m = ms.get(j);
+  w.ntiles = msg_tiles(w.m.len, ts.tile, ts.by_tile, ts.small_max);
+  const int64_t w0 = __ldg(weight_off + j);
+  w.k = ts.by_step(w_begin - w0 + ts.tile + kTileCost - 1);
+  w.wk = w0 + w.k * (ts.tile + kTileCost);
+  w.w_end = w_end;
 }
 
-// The view of tile t (t >= the previous tile asked for).
+// The view of the walk's next tile; false when the warp's share is done.
 template <class Msgs>
-__device__ __forceinline__ TileView walk_view(WalkState& w, const Msgs& ms,
-                                              const int64_t* tile_off, int64_t t, int64_t tile,
-                                              int64_t out_tile) {
-  while (t >= w.t_end) {
-    ++w.j;
-    walk_load(w, ms, tile_off);
+__device__ __forceinline__ bool walk_next(WalkState& w, const Msgs& ms, int64_t nmsg,
+                                          const TileShape& ts, TileView& v) {
+  const int64_t tile = ts.tile;
+  while (w.k >= w.ntiles) {  // on to the next message with tiles
+    // tile k (= ntiles) would start where the message's weight ends, less
+    // the last tile's shortfall from a whole tile
+    w.wk -= w.ntiles ? w.ntiles * tile - w.m.len : 0;
+    if (++w.j >= nmsg) return false;
+    w.m = ms.get(w.j);
+    w.ntiles = msg_tiles(w.m.len, tile, ts.by_tile, ts.small_max);
+    w.k = 0;
   }
+  if (w.wk >= w.w_end) return false;
   const Msg m = w.m;
-  const int64_t k = t - w.t_first;
-  TileView v;
+  const int64_t k = w.k++;
+  w.wk += tile + kTileCost;
   v.msrc = m.src;
   v.mout = m.out;
-  v.lo = m.lo;
-  v.hi = m.hi;
-  v.dst = m.out + k * out_tile;
+  v.lo = ms.lo(m);
+  v.hi = ms.hi(m);
+  v.dst = m.out + k * ts.out_tile;
   v.t0 = k * tile;
   v.mlen = m.len;
   v.j = w.j;
@@ -366,7 +361,7 @@ __device__ __forceinline__ TileView walk_view(WalkState& w, const Msgs& ms,
   v.o = (uint32_t)(s & 15u);
   v.ia = v.o ? 16u : 0u;
   v.ib = b > a ? v.ia + (uint32_t)(b - a) : v.ia;
-  return v;
+  return true;
 }
 
 // Issues the bulk copy of a tile's interior into its input stage (one lane;
@@ -898,10 +893,10 @@ __device__ __noinline__ void code_short_messages(Msgs ms, int64_t nmsg, int64_t 
     const Msg m = ms.get(j);
     if (DECODE) {
       decode_message(m.src, m.len, m.out, table,
-                     reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j, flags, m.lo,
-                     m.hi);
+                     reinterpret_cast<unsigned long long*>(first_bad + j), outlen + j, flags,
+                     ms.lo(m), ms.hi(m));
     } else {
-      encode_message(m.src, m.len, m.out, table, flags, m.lo, m.hi);
+      encode_message(m.src, m.len, m.out, table, flags, ms.lo(m), ms.hi(m));
     }
   }
 }
@@ -919,16 +914,24 @@ __host__ __device__ __forceinline__ uint32_t warp_smem_bytes(int decode, int64_t
   return stages * stage_in_bytes(tile) + (decode ? (uint32_t)out_tile_bytes(1, tile) + 32u : 0u);
 }
 
-// The persistent kernel of both directions: warp w of the grid's G warps
-// owns tiles [w*T/G, (w+1)*T/G) of the T = tile_off[nmsg] tiles, in order.
-// Lane 0 of the warp computes each tile's view once, when it issues the
-// tile's copy, and leaves it beside the stage.
+// The share [w_begin, w_end) of the batch's weight that warp w of the
+// grid's nw warps codes.
+__device__ __forceinline__ void warp_share(const int64_t* weight_off, int64_t nmsg, int64_t w,
+                                           int64_t nw, int64_t& w_begin, int64_t& w_end) {
+  const int64_t total = __ldg(weight_off + nmsg);
+  w_begin = total * w / nw;
+  w_end = total * (w + 1) / nw;
+}
+
+// The persistent kernel of both directions with staged tiles. Lane 0 of a
+// warp walks its tiles, issuing each one's bulk copy `stages` tiles ahead
+// and leaving its view beside the stage; the warp codes the staged tiles
+// in order.
 template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off,
-                 const int64_t* __restrict__ weight_off, int64_t tile, uint32_t stages,
-                 int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
-                 int64_t small_max) {
+    k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ weight_off, TileShape ts,
+                 uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
+                 uint32_t flags) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
@@ -945,34 +948,40 @@ __global__ void __launch_bounds__(NT)
   } else {
     init_tables(table, nullptr, flags & kFlagUrl);
   }
-  const int64_t out_tile = out_tile_bytes(DECODE, tile);
-  const uint32_t in_b = stage_in_bytes(tile);
-  uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, tile, S);
+  const uint32_t in_b = stage_in_bytes(ts.tile);
+  uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, ts.tile, S);
   uint8_t* obase = wbase + S * in_b;  // decode: the output buffer
 
-  int64_t t_begin, t_end, j_begin;
-  warp_tile_range(tile_off, weight_off, nmsg, tile, (int64_t)blockIdx.x * (NT / 32) + warp,
-                  (int64_t)gridDim.x * (NT / 32), lane, t_begin, t_end, j_begin);
+  int64_t w_begin, w_end;
+  warp_share(weight_off, nmsg, (int64_t)blockIdx.x * (NT / 32) + warp,
+             (int64_t)gridDim.x * (NT / 32), w_begin, w_end);
   Msgs ms = msgs;
   ms.prepare(nmsg);
   WalkState& walk = walks[warp];  // used by lane 0
-  if (lane == 0 && t_begin < t_end) {  // the first tiles' copies go out first
-    walk.j = j_begin;
-    walk_load(walk, ms, tile_off);
-    for (uint32_t s = 0; s < S && t_begin + s < t_end; ++s) {
-      meta[warp][s] = walk_view(walk, ms, tile_off, t_begin + s, tile, out_tile);
-      issue_tile(meta[warp][s], wbase + s * in_b, &full[warp][s]);
+  uint32_t primed = 0;            // tiles issued before the loop (lane 0)
+  bool more = false;              // the walk may have further tiles (lane 0)
+  if (w_begin < w_end) {          // the first tiles' copies go out first
+    const int64_t j0 = owner_of_warp(weight_off, nmsg, w_begin, lane);
+    if (lane == 0) {
+      walk_begin(walk, ms, weight_off, j0, w_begin, w_end, ts);
+      TileView v;
+      while (primed < S && walk_next(walk, ms, nmsg, ts, v)) {
+        meta[warp][primed] = v;
+        issue_tile(v, wbase + primed * in_b, &full[warp][primed]);
+        ++primed;
+      }
+      more = primed == S;
     }
   }
   // short messages (no tiles) while those copies are in flight
-  if (small_max > 0)
-    code_short_messages<DECODE>(ms, nmsg, small_max, table, first_bad, outlen, flags);
-  if (t_begin >= t_end) return;
+  if (ts.small_max > 0)
+    code_short_messages<DECODE>(ms, nmsg, ts.small_max, table, first_bad, outlen, flags);
+  uint32_t pending = __shfl_sync(0xFFFFFFFFu, primed, 0);  // tiles issued, not yet coded
+  if (pending == 0) return;
 
-  bool timed_out = false;
+  bool timed_out = false, first = true;
   uint32_t s = 0, phase = 0;
-  int64_t t = t_begin;
-  for (; t < t_end; ++t) {
+  while (pending > 0) {
     uint8_t* in = wbase + s * in_b;
     const bool ok = mbar_wait_backoff(&full[warp][s], phase);
     if (__any_sync(0xFFFFFFFFu, !ok)) {
@@ -982,19 +991,28 @@ __global__ void __launch_bounds__(NT)
     const TileView v = meta[warp][s];
     if (DECODE) {
       // the previous tile's bulk store has finished reading the output buffer
-      if (lane == 0 && t > t_begin) bulk_wait_read(0);
+      if (lane == 0 && !first) bulk_wait_read(0);
       __syncwarp();
       decode_tile<false>(v, in, obase, table,
-                  reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j, lane, flags);
+                         reinterpret_cast<unsigned long long*>(first_bad + v.j), outlen + v.j,
+                         lane, flags);
     } else {
       encode_tile<false>(v, in, table, lane, flags);
       fence_proxy_async_smem();  // the stage's reads come before its next copy
       __syncwarp();
     }
-    if (lane == 0 && t + S < t_end) {
-      meta[warp][s] = walk_view(walk, ms, tile_off, t + S, tile, out_tile);
-      issue_tile(meta[warp][s], in, &full[warp][s]);
+    uint32_t issued = 0;
+    if (lane == 0 && more) {
+      TileView nv;
+      more = walk_next(walk, ms, nmsg, ts, nv);
+      if (more) {
+        meta[warp][s] = nv;
+        issue_tile(nv, in, &full[warp][s]);
+        issued = 1;
+      }
     }
+    pending = pending - 1 + __shfl_sync(0xFFFFFFFFu, issued, 0);
+    first = false;
     if (++s == S) {
       s = 0;
       phase ^= 1u;
@@ -1003,7 +1021,7 @@ __global__ void __launch_bounds__(NT)
   if (timed_out && lane == 0) {
     atomicOr(&g_batch_fault, 1u);
     // wait (bounded) for the copies still in flight into this warp's stages
-    for (uint32_t i = 0; i < S && t + i < t_end; ++i) {
+    for (uint32_t i = 0; i < pending; ++i) {
       mbar_wait_bounded(&full[warp][s], phase, 500000000ull);
       if (++s == S) {
         s = 0;
@@ -1014,17 +1032,15 @@ __global__ void __launch_bounds__(NT)
   if (DECODE && lane == 0) bulk_wait_all();
 }
 
-// The same persistent walk without staging: every lane keeps the walk in
-// registers (one warp-instruction each, as on one lane), and the tiles'
-// units move straight between global memory and registers, so a warp needs
-// no shared memory, barrier or copy engine, and a tile may be longer than a
-// stage could hold.
+// The same walk without staging: every lane keeps the walk in registers
+// (one warp-instruction each, as on one lane), and the tiles' units move
+// straight between global memory and registers, so a warp needs no shared
+// memory, barrier or copy engine, and a tile may be longer than a stage
+// could hold.
 template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
-    k_batch_direct(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ tile_off,
-                   const int64_t* __restrict__ weight_off, int64_t tile,
-                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
-                   int64_t small_max) {
+    k_batch_direct(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ weight_off, TileShape ts,
+                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags) {
   __shared__ uint8_t table[DECODE ? 256 : 64];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (DECODE) {
@@ -1032,20 +1048,20 @@ __global__ void __launch_bounds__(NT)
   } else {
     init_tables(table, nullptr, flags & kFlagUrl);
   }
-  const int64_t out_tile = out_tile_bytes(DECODE, tile);
-  int64_t t_begin, t_end, j_begin;
-  warp_tile_range(tile_off, weight_off, nmsg, tile, (int64_t)blockIdx.x * (NT / 32) + warp,
-                  (int64_t)gridDim.x * (NT / 32), lane, t_begin, t_end, j_begin);
+  int64_t w_begin, w_end;
+  warp_share(weight_off, nmsg, (int64_t)blockIdx.x * (NT / 32) + warp,
+             (int64_t)gridDim.x * (NT / 32), w_begin, w_end);
   Msgs ms = msgs;
   ms.prepare(nmsg);
-  if (small_max > 0)
-    code_short_messages<DECODE>(ms, nmsg, small_max, table, first_bad, outlen, flags);
-  if (t_begin >= t_end) return;
+  if (ts.small_max > 0)
+    code_short_messages<DECODE>(ms, nmsg, ts.small_max, table, first_bad, outlen, flags);
+  if (w_begin >= w_end) return;
   WalkState walk;
-  walk.j = j_begin;
-  walk_load(walk, ms, tile_off);
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    TileView v = walk_view(walk, ms, tile_off, t, tile, out_tile);
+  walk_begin(walk, ms, weight_off, owner_of_warp(weight_off, nmsg, w_begin, lane), w_begin, w_end,
+             ts);
+  for (;;) {
+    TileView v;
+    if (!walk_next(walk, ms, nmsg, ts, v)) break;
     v.o = v.ia = v.ib = 0u;  // nothing staged
     if (DECODE) {
       decode_tile<true>(v, nullptr, nullptr, table,
@@ -1091,31 +1107,32 @@ size_t batch_smem_bytes(int decode, const BatchConfig& c) {
 
 size_t batch_scratch_bytes(int64_t nmsg) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  return (size_t)(nmsg + 1) * 16 + (size_t)std::max<int64_t>(nparts, 1) * 24;
+  return (size_t)(nmsg + 1) * 8 + (size_t)std::max<int64_t>(nparts, 1) * 16;
 }
 
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
-                          int64_t* tile_off, int64_t* weight_off, int64_t tile, void* scratch_parts,
+                          int64_t* weight_off, int64_t tile, void* scratch_parts,
                           int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
                           uint32_t flags, int64_t small_max) {
   const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  int64_t* parts = static_cast<int64_t*>(scratch_parts);
+  int64_t* part_out = static_cast<int64_t*>(scratch_parts);
+  int64_t* part_weight = part_out + std::max<int64_t>(nparts, 1);
   if (nparts > 0) {
     k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
-                                                                small_max, out_off, tile_off,
-                                                                weight_off, parts, nparts);
-    k_scan_parts<<<1, kScanThreads, 0, stream>>>(parts, nparts);
+                                                                small_max, out_off, weight_off,
+                                                                part_out, part_weight);
+    k_scan_parts<<<1, kScanThreads, 0, stream>>>(part_out, part_weight, nparts);
   }
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
-  k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, tile_off, weight_off, parts,
-                                                   nparts, first_bad, outlen);
+  k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, weight_off, part_out,
+                                                   part_weight, first_bad, outlen);
   return cudaGetLastError();
 }
 
 namespace {
 template <int NT, class Msgs>
-cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
-                        const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* weight_off,
+                        int32_t* status, int64_t* first_bad,
                         int64_t* outlen, const BatchConfig& cfg, const DeviceInfo* di,
                         uint32_t flags, cudaStream_t stream, int64_t small_max) {
   const bool direct = cfg.kernel == 2;
@@ -1135,24 +1152,22 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const int bps = cfg.blocks_per_sm > 0 ? std::min(fit, cfg.blocks_per_sm) : fit;
   const int grid = di->sm_count * bps;
   const uint32_t stages = (uint32_t)cfg.stages;
+  const TileShape ts{cfg.tile, out_tile_bytes(decode, cfg.tile), small_max, DivBy::of(cfg.tile),
+                     DivBy::of(cfg.tile + kTileCost)};
   if (direct) {
     if (decode) {
-      k_batch_direct<NT, 1, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, weight_off,
-                                                           cfg.tile, first_bad, outlen, flags,
-                                                           small_max);
+      k_batch_direct<NT, 1, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, weight_off, ts, first_bad,
+                                                           outlen, flags);
     } else {
-      k_batch_direct<NT, 0, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, tile_off, weight_off,
-                                                           cfg.tile, nullptr, nullptr, flags,
-                                                           small_max);
+      k_batch_direct<NT, 0, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, weight_off, ts, nullptr,
+                                                           nullptr, flags);
     }
   } else if (decode) {
-    k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, weight_off,
-                                                          cfg.tile, stages, first_bad, outlen,
-                                                          flags, small_max);
+    k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,
+                                                          first_bad, outlen, flags);
   } else {
-    k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, tile_off, weight_off,
-                                                          cfg.tile, stages, nullptr, nullptr,
-                                                          flags, small_max);
+    k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,
+                                                          nullptr, nullptr, flags);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !decode) return e;
@@ -1163,8 +1178,8 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
 }
 
 template <class Msgs>
-cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* tile_off,
-                            const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* weight_off,
+                            int32_t* status, int64_t* first_bad,
                             int64_t* outlen, const BatchConfig& cfg, uint32_t flags,
                             cudaStream_t stream, int64_t small_max = 0) {
   cudaError_t e;
@@ -1172,21 +1187,21 @@ cudaError_t launch_work_any(int decode, const Msgs& msgs, int64_t nmsg, const in
   if (!di) return e;
   switch (cfg.threads) {
     case 128:
-      return launch_work<128>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
-                              cfg, di, flags, stream, small_max);
+      return launch_work<128>(decode, msgs, nmsg, weight_off, status, first_bad, outlen, cfg, di,
+                              flags, stream, small_max);
     case 512:
-      return launch_work<512>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
-                              cfg, di, flags, stream, small_max);
+      return launch_work<512>(decode, msgs, nmsg, weight_off, status, first_bad, outlen, cfg, di,
+                              flags, stream, small_max);
     default:
-      return launch_work<256>(decode, msgs, nmsg, tile_off, weight_off, status, first_bad, outlen,
-                              cfg, di, flags, stream, small_max);
+      return launch_work<256>(decode, msgs, nmsg, weight_off, status, first_bad, outlen, cfg, di,
+                              flags, stream, small_max);
   }
 }
 }  // namespace
 
 cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
-                              const int64_t* tile_off, const int64_t* weight_off,
-                              int32_t* status, int64_t* first_bad, int64_t* outlen,
+                              const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+                              int64_t* outlen,
                               const BatchConfig& cfg, bool init_results, cudaStream_t stream,
                               uint32_t flags) {
   if (decode && init_results) {
@@ -1195,21 +1210,21 @@ cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uin
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, tile_off, weight_off, status,
-                         first_bad, outlen, cfg, flags, stream);
+  return launch_work_any(decode, DescMsgs{desc, dst}, nmsg, weight_off, status, first_bad, outlen,
+                         cfg, flags, stream);
 }
 
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg) {
   const int64_t small_max = cfg.kernel != 1 ? batch_small_max(a.decode) : 0;
-  cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.tile_off, a.weight_off,
-                                cfg.tile, a.parts, a.decode ? a.first_bad : nullptr,
+  cudaError_t e = batch_offsets(a.decode, a.in_off, a.nmsg, a.out_off, a.weight_off, cfg.tile,
+                                a.parts, a.decode ? a.first_bad : nullptr,
                                 a.decode ? a.outlen : nullptr, a.stream, a.flags, small_max);
   if (e != cudaSuccess) return e;
   // src_hi (the end of the packed input, in_off[nmsg]) is read on the device
   PackedMsgs msgs{a.src, a.in_off, a.dst, a.out_off, nullptr};
   // short messages go one thread each at the start of the tile kernel
-  return launch_work_any(a.decode, msgs, a.nmsg, a.tile_off, a.weight_off, a.status, a.first_bad,
-                         a.outlen, cfg, a.flags, a.stream, small_max);
+  return launch_work_any(a.decode, msgs, a.nmsg, a.weight_off, a.status, a.first_bad, a.outlen,
+                         cfg, a.flags, a.stream, small_max);
 }
 
 // Longest messages (input bytes / characters) coded one thread each by

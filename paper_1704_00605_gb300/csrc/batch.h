@@ -28,7 +28,6 @@ struct BatchArgs {
   int64_t nmsg = 0;
   uint8_t* dst = nullptr;
   int64_t* out_off = nullptr;
-  int64_t* tile_off = nullptr;    // scratch: nmsg + 1 entries
   int64_t* weight_off = nullptr;  // scratch: nmsg + 1 entries
   void* parts = nullptr;          // scratch: block totals of the scan
   int32_t* status = nullptr;    // decode only
@@ -52,40 +51,35 @@ struct MsgDesc {
 // t tiles weighs len + t * kBatchTileCost (0 with no tiles).
 constexpr int64_t kBatchTileCost = 1024;
 
-// Codes a batch described by host-built descriptors, tile offsets
-// (tile_off[j] = sum over earlier messages of ceil(len / cfg.tile)) and
-// weight offsets (the same sums of the weights above), with no device scan:
-// the persistent tile kernel (+ the decode finish kernel, + an
-// initialisation of first_bad/outlen when init_results). weight_off may be
-// null: the warps then take equal tile counts.
+// Codes a batch described by host-built descriptors and weight offsets
+// (weight_off[j] = sum over earlier messages of their weights above, every
+// message of len > 0 being cut into ceil(len / cfg.tile) tiles), with no
+// device scan: the persistent tile kernel (+ the decode finish kernel, + an
+// initialisation of first_bad/outlen when init_results).
 cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uint8_t* dst,
-                              const int64_t* tile_off, const int64_t* weight_off,
-                              int32_t* status, int64_t* first_bad, int64_t* outlen,
-                              const BatchConfig& cfg, bool init_results, cudaStream_t stream,
-                              uint32_t flags = 0);
+                              const int64_t* weight_off, int32_t* status, int64_t* first_bad,
+                              int64_t* outlen, const BatchConfig& cfg, bool init_results,
+                              cudaStream_t stream, uint32_t flags = 0);
 
-// Bytes of scratch a batch of nmsg messages needs (tile_off, weight_off and
-// the scan's block totals).
+// Bytes of scratch a batch of nmsg messages needs (weight_off and the
+// scan's block totals).
 size_t batch_scratch_bytes(int64_t nmsg);
 
 // Splits a scratch block of batch_scratch_bytes(nmsg) into its arrays.
-inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** tile_off,
-                                int64_t** weight_off, void** parts) {
-  *tile_off = static_cast<int64_t*>(scratch);
-  *weight_off = *tile_off + (nmsg + 1);
+inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** weight_off, void** parts) {
+  *weight_off = static_cast<int64_t*>(scratch);
   *parts = *weight_off + (nmsg + 1);
 }
 
-// Output offsets of a batch, with its tile offsets and weight offsets (the
-// prefix sums of each message's tile count and of its length plus a fixed
-// cost per tile, by which the tile kernels split the work among warps);
+// Output offsets of a batch, and its weight offsets (the prefix sums of the
+// weights above, by which the tile kernels split the work among warps);
 // first_bad/outlen (decode) are initialised when non-null.
 // small_max > 0: messages of at most small_max bytes / characters get no
 // tiles (threads code them one each).
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
-                          int64_t* tile_off, int64_t* weight_off, int64_t tile, void* parts,
-                          int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
-                          uint32_t flags = 0, int64_t small_max = 0);
+                          int64_t* weight_off, int64_t tile, void* parts, int64_t* first_bad,
+                          int64_t* outlen, cudaStream_t stream, uint32_t flags = 0,
+                          int64_t small_max = 0);
 int64_t batch_small_max(int decode);
 
 // Offsets + the persistent tile kernel (+ the decode finish kernel).

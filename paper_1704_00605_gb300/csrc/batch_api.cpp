@@ -63,7 +63,7 @@ int run_batch(BatchArgs a) {
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(a.nmsg), a.stream);
   if (e != cudaSuccess) return cuda_status(e, "batch: scratch");
-  batch_scratch_split(scratch, a.nmsg, &a.tile_off, &a.weight_off, &a.parts);
+  batch_scratch_split(scratch, a.nmsg, &a.weight_off, &a.parts);
   const BatchConfig cfg = tuned_batch_config(a.decode, a.nmsg);
   e = batch_launch(a, cfg);
   cudaError_t ef = cudaFreeAsync(scratch, a.stream);
@@ -89,11 +89,11 @@ int b64_batch_out_offsets_ex(int decode, const int64_t* in_off, int64_t nmsg, in
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, batch_scratch_bytes(nmsg), s);
   if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets: scratch");
-  int64_t *tile_off, *weight_off;
+  int64_t* weight_off;
   void* parts;
-  batch_scratch_split(scratch, nmsg, &tile_off, &weight_off, &parts);
-  e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, tile_off, weight_off, 1 << 20, parts,
-                    nullptr, nullptr, s, (uint32_t)flags);
+  batch_scratch_split(scratch, nmsg, &weight_off, &parts);
+  e = batch_offsets(decode ? 1 : 0, in_off, nmsg, out_off, weight_off, 1 << 20, parts, nullptr,
+                    nullptr, s, (uint32_t)flags);
   cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e == cudaSuccess) e = ef;
   if (e != cudaSuccess) return cuda_status(e, "batch_out_offsets");

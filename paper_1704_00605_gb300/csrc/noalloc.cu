@@ -14,7 +14,7 @@
 //   - at most kNoAllocMaxMsgs messages per call (larger batches are rejected
 //     with B64_ERR_ARG before anything is enqueued);
 //   - the array is loaded with the library on every GPU that uses it and
-//     stays allocated there until the process exits (about 1 MiB);
+//     stays allocated there until the process exits (about 576 KiB);
 //   - every call on a device uses the same array, so two calls whose work
 //     overlaps on the GPU (different streams, no ordering) race and give
 //     wrong results: order them on one stream or with events;
@@ -32,7 +32,7 @@ namespace gb64 {
 namespace {
 
 constexpr int64_t kNoAllocMaxMsgs = 65536;
-constexpr size_t kNoAllocScratchBytes = 1040u << 10;
+constexpr size_t kNoAllocScratchBytes = 576u << 10;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -109,7 +109,7 @@ extern "C" int b64_decode_batch_noalloc(const char* src, const int64_t* in_off, 
   a.first_bad = first_bad;
   a.outlen = outlen;
   a.stream = reinterpret_cast<cudaStream_t>(stream);
-  batch_scratch_split(scratch, nmsg, &a.tile_off, &a.weight_off, &a.parts);
+  batch_scratch_split(scratch, nmsg, &a.weight_off, &a.parts);
   e = batch_launch(a, tuned_batch_config(1, nmsg));
   if (e != cudaSuccess) return cuda_status(e, "decode_batch_noalloc: launch");
   return B64_OK;

@@ -100,7 +100,7 @@ struct Request {
 // Block layout of one batch (offsets from the block start). The first
 // h2d_bytes are copied from the host; the d2h region holds decode results.
 struct Layout {
-  uint64_t desc, tile_off, weight_off, first_bad, outlen, status, out, total;
+  uint64_t desc, weight_off, first_bad, outlen, status, out, total;
   uint64_t h2d_bytes, d2h_off, d2h_bytes;
 };
 
@@ -108,8 +108,7 @@ Layout layout_for(int64_t n, int64_t out_bytes, int kind) {
   auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
   Layout L;
   L.desc = 0;
-  L.tile_off = L.desc + (uint64_t)n * sizeof(MsgDesc);
-  L.weight_off = L.tile_off + (uint64_t)(n + 1) * 8;
+  L.weight_off = L.desc + (uint64_t)n * sizeof(MsgDesc);
   L.first_bad = L.weight_off + (uint64_t)(n + 1) * 8;
   L.outlen = L.first_bad + (uint64_t)n * 8;
   L.status = L.outlen + (uint64_t)n * 8;
@@ -263,14 +262,12 @@ cudaError_t launch_batch(const Batch& B, Slot& sl, uint8_t* arena_base) {
   const int64_t n = (int64_t)B.members.size();
   uint8_t* blk = arena_base + B.block;
   MsgDesc* h_desc = reinterpret_cast<MsgDesc*>(sl.host + B.L.desc);
-  int64_t* h_tile = reinterpret_cast<int64_t*>(sl.host + B.L.tile_off);
   int64_t* h_weight = reinterpret_cast<int64_t*>(sl.host + B.L.weight_off);
-  h_tile[0] = h_weight[0] = 0;
+  h_weight[0] = 0;
   for (int64_t j = 0; j < n; ++j) {
     const Member& m = B.members[j];
     h_desc[j] = MsgDesc{m.src, m.len, m.out_off};
-    const int64_t tiles = (m.len + B.cfg.tile - 1) / B.cfg.tile;
-    h_tile[j + 1] = h_tile[j] + tiles;
+    const int64_t tiles = m.len > 0 ? (m.len + B.cfg.tile - 1) / B.cfg.tile : 0;
     h_weight[j + 1] = h_weight[j] + (tiles ? m.len + tiles * kBatchTileCost : 0);
   }
   if (B.kind) {
@@ -284,8 +281,7 @@ cudaError_t launch_batch(const Batch& B, Slot& sl, uint8_t* arena_base) {
   cudaError_t e = cudaMemcpyAsync(blk, sl.host, B.L.h2d_bytes, cudaMemcpyHostToDevice, sl.stream);
   if (e != cudaSuccess) return e;
   e = batch_launch_desc(B.kind, reinterpret_cast<const MsgDesc*>(blk + B.L.desc), n,
-                        blk + B.L.out, reinterpret_cast<const int64_t*>(blk + B.L.tile_off),
-                        reinterpret_cast<const int64_t*>(blk + B.L.weight_off),
+                        blk + B.L.out, reinterpret_cast<const int64_t*>(blk + B.L.weight_off),
                         reinterpret_cast<int32_t*>(blk + B.L.status),
                         reinterpret_cast<int64_t*>(blk + B.L.first_bad),
                         reinterpret_cast<int64_t*>(blk + B.L.outlen), B.cfg, false, sl.stream);

@@ -347,7 +347,7 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
   ba.status = st;
   ba.first_bad = fb;
   ba.outlen = ol;
-  if (batch) batch_scratch_split(scratch, nmsg, &ba.tile_off, &ba.weight_off, &ba.parts);
+  if (batch) batch_scratch_split(scratch, nmsg, &ba.weight_off, &ba.parts);
   if (decode) {  // decode input = encoding of the random bytes
     if (batch) {
       BatchArgs ea = ba;
