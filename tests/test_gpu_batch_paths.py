@@ -241,3 +241,31 @@ def test_lengths_around_the_short_message_limit(gb64, oracle, flags):
     for mode in MODES:
         with kernel_choice(gb64, mode):
             _check_decode(oracle, allc, coff, _decode(gb64, allc, coff, 0, flags), flags)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_weight_split_edge_cases(gb64, oracle, mode):
+    """The warps' equal shares of the batch weight (bytes + a fixed cost per
+    tile): batches whose total weight is below the number of warps (most
+    shares empty), one huge message among tiny ones (its tiles spread over
+    many warps), and lengths at tile boundaries, at the short-message limit
+    and at 0 between them; every message codes exactly."""
+    kernel, enc_rows, dec_rows = mode
+    rng = np.random.default_rng(77 + kernel + enc_rows)
+    enc_tile, dec_tile = 384 * enc_rows, 512 * dec_rows
+    cases = [
+        np.array([257, 258, 259], dtype=np.int64),                      # 3 small tiles, most warps idle
+        np.array([0, 0, 345, 0], dtype=np.int64),
+        np.concatenate([rng.integers(0, 40, 5000), [3 << 20], rng.integers(0, 40, 5000)]),
+        np.array([k * enc_tile + d for k in (1, 2, 3) for d in (-1, 0, 1)] * 7 + [0] * 5),
+        np.array([k * dec_tile // 4 * 3 + d for k in (1, 2, 5) for d in (-2, -1, 0, 1, 2)] * 5),
+    ]
+    with kernel_choice(gb64, mode):
+        for lens in cases:
+            lens = lens.astype(np.int64)
+            off = W.offsets_from_lengths(lens)
+            data = W.uniform_bytes(int(off[-1]), int(lens.sum() % 1000) + 3)
+            exp, exp_off = oracle.encode_batch(data, off)
+            out, out_off = _encode(gb64, data, off, 0)
+            assert np.array_equal(out_off, exp_off) and np.array_equal(out, exp), lens[:8]
+            _check_decode(oracle, exp, exp_off, _decode(gb64, exp, exp_off, 0), 0)
