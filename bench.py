@@ -48,7 +48,8 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=1200)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["large", "batched", "serve", "sweep"], default="large")
+    p.add_argument("--config", choices=["large", "batched", "serve", "sweep", "variants"],
+                   default="large")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched and serving sub-measurements of the default line")
     p.add_argument("--no-e2e", action="store_true")
@@ -787,6 +788,20 @@ def sweep_line(args, d: Dist):
     }
 
 
+def variants_line(args, d: Dist):
+    v = run_variants(args, d)
+    ws = v["whitespace"]
+    return {
+        "metric": "decode input GB/s with whitespace removal (Appendix B, MIME lines)",
+        "value": ws["decode_input_gbs"], "unit": "GB/s", "n_gpus": d.world, "steps": 10,
+        "warmup": 1, "ms_per_step": ws["decode_us"] / 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic: uniform random bytes",
+        "config": {"workload": "variant flags on 256 MiB; whitespace removal on its MIME-wrapped "
+                               "encoding (CRLF after every 76 characters)"},
+        "variants_256mib": v,
+    }
+
+
 # ------------------------------------------------------ reference arm
 def run_reference(args, d: Dist):
     """The CPU oracle as it stands, on the host cores, on bounded samples of
@@ -838,6 +853,8 @@ def main(argv=None):
         line = serve_line(args, d)
     elif args.config == "sweep":
         line = sweep_line(args, d)
+    elif args.config == "variants":
+        line = variants_line(args, d)
     else:
         line = run_large(args, d)
         if not args.small and not args.no_extras:

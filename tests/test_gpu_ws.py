@@ -100,6 +100,32 @@ def test_degenerate(gb64, oracle):
         check(gb64, oracle, s, SKIP_WS)
 
 
+def test_whitespace_runs_across_tiles(gb64, oracle):
+    """The decode reads the kept characters just after its tile (the rest of
+    a unit, or the final quads) from the following tiles: runs of
+    whitespace longer than a tile (16,384 characters), tiles that keep a
+    single character, errors and final groups among those characters."""
+    from paper_1704_00605_gb300.workloads import NON_ALPHABET_NON_PAD
+
+    tile = 16384
+    rng = np.random.default_rng(21)
+    e = base64.b64encode(rng.integers(0, 256, 3001, dtype=np.uint8).tobytes())
+    bad = bytes([[b for b in NON_ALPHABET_NON_PAD.tolist() if b not in WS][7]])
+    cases = []
+    for cut in (1, 3, 15, 16, 17, 1001, len(e) - 3, len(e) - 1):
+        for gap in (tile - 1, 3 * tile + 5):
+            cases.append(e[:cut] + b" " * gap + e[cut:])
+    sparse = b"".join(e[i:i + 1] + b"\n" * (tile - 1) for i in range(40)) + e[40:]
+    cases += [sparse, b" " * (2 * tile - 7) + e[:9] + b" " * tile + e[9:],
+              b"".join(e[i:i + 1] + b" " * (tile - 1) for i in range(len(e) - 6, len(e)))]
+    for k, s in enumerate(cases):
+        check(gb64, oracle, s, SKIP_WS, off=k % 3)
+        t = bytearray(s)
+        kept = [i for i, c in enumerate(t) if c not in WS]
+        t[kept[min(len(kept) - 1, 17 + k)]] = bad[0]  # an error among the halo's characters
+        check(gb64, oracle, bytes(t), SKIP_WS)
+
+
 def test_rejected_where_not_supported(gb64):
     import torch
 
