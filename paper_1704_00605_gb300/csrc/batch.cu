@@ -243,16 +243,17 @@ struct DescMsgs {
 };
 
 // ------------------------------------------------------ warp pipeline
-// Every warp walks its own range of tiles (see WalkState below). Tile k of
-// message j holds input bytes [t0, t0 + len) of j, t0 = k * tile, len <= tile. The tile's
-// 16-byte-aligned interior is copied into the warp's input stage by one bulk
-// copy, issued `stages` tiles ahead; stage position o + i holds input byte
-// t0 + i, o being the tile start's address mod 16, so positions [ia, ib)
-// are the copied ones. Units whose bytes reach outside [ia, ib) read global
-// memory instead. Every unit's output goes to the warp's output stage at
-// position o2 + i for output byte i (o2 = the output start's address mod
-// 16); the aligned interior of the tile's output leaves by one bulk store,
-// its two ragged ends (at most 15 bytes each) by byte stores.
+// Every warp walks its own share of the tiles (see WalkState below). Tile k
+// of message j holds input bytes [t0, t0 + len) of j, t0 = k * tile,
+// len <= tile. Staged, the tile's 16-byte-aligned interior is copied into
+// the warp's input stage by one bulk copy, issued `stages` tiles ahead;
+// stage position o + i holds input byte t0 + i, o being the tile start's
+// address mod 16, so positions [ia, ib) are the copied ones. Units whose
+// bytes reach outside [ia, ib) read global memory instead. A staged decode
+// puts output byte i of the tile at position o2 + i of the warp's output
+// buffer (o2 = the output start's address mod 16); the aligned interior
+// leaves by one bulk store, the two ragged ends (at most 15 bytes each) by
+// byte stores. Encoding, and unstaged, outputs go straight to global memory.
 struct TileView {
   const uint8_t* msrc;  // the message's input and output
   uint8_t* mout;
@@ -267,15 +268,6 @@ struct TileView {
   uint32_t ia, ib;
 };
 
-// A warp's walk over its tiles. Warp w of the grid's nw warps owns the
-// weight [W*w/nw, W*(w+1)/nw) of the batch's total W and takes the tiles
-// that start in it, tile k of message j starting at weight weight_off[j] +
-// k * (tile + kTileCost): equal shares of bytes and tiles, whatever the mix
-// of lengths (equal tile counts would not be equal work, the last tile of
-// a message being short). The walk finds the message of its first tile by
-// a search, then moves forward one message at a time, counting each one's
-// tiles from its length as the scan did; the offsets arrays are read only
-// when it enters the next message.
 // The tile geometry of a launch.
 struct TileShape {
   int64_t tile;       // input bytes / characters of a whole tile
@@ -285,6 +277,15 @@ struct TileShape {
   DivBy by_step;      // division by tile + kTileCost
 };
 
+// A warp's walk over its tiles. Warp w of the grid's nw warps owns the
+// weight [W*w/nw, W*(w+1)/nw) of the batch's total W and takes the tiles
+// that start in it, tile k of message j starting at weight weight_off[j] +
+// k * (tile + kTileCost): equal shares of bytes and tiles, whatever the mix
+// of lengths (equal tile counts would not be equal work, the last tile of
+// a message being short). The walk finds the message of its first tile by
+// a search, then moves forward one message at a time, counting each one's
+// tiles from its length as the scan did; the offsets arrays are read only
+// when it enters the next message.
 struct WalkState {
   Msg m;
   int64_t j;       // current message
@@ -881,8 +882,8 @@ __device__ __noinline__ void code_short_messages(Msgs ms, int64_t nmsg, int64_t 
   }
 }
 
-// Shared memory of a warp: `stages` input stages, and (decode) two output
-// buffers, used by alternate tiles.
+// Shared memory of a warp (staged tiles): `stages` input stages and, for
+// decode, one output buffer.
 __host__ __device__ __forceinline__ uint32_t stage_in_bytes(int64_t tile) {
   return (uint32_t)tile + 32u;
 }

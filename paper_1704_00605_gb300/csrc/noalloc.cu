@@ -1,6 +1,6 @@
 // Batched decode that allocates no memory at all.
 //
-// b64_decode_batch takes its scratch (the tile offsets and the scan's block
+// b64_decode_batch takes its scratch (the weight offsets and the scan's block
 // totals) from the stream-ordered allocator on every call. Some callers
 // cannot do that: code that runs under a fixed device-memory budget or with
 // its own pool (a serving loop that admits requests by free memory), hot

@@ -3,14 +3,14 @@
 // Requests name a device-resident payload (pointer + length) and arrive at
 // any time (b64_server_submit, thread-safe). One engine thread
 //   - admits requests by device memory: every batch takes one block of a
-//     fixed arena (the memory budget) for its descriptors, tile offsets,
+//     fixed arena (the memory budget) for its descriptors, weight offsets,
 //     per-message results and outputs; a batch that does not fit waits until
 //     earlier outputs are released (counted as a memory wait);
 //   - forms a batch per free stream slot from the pending requests of one
 //     kind (the kind whose oldest request is oldest), up to max_batch_msgs
 //     requests and max_batch_bytes payload bytes, so requests that arrive
 //     while other batches run join the next batch (continuous batching);
-//   - builds the batch's message descriptors and tile offsets on the host
+//   - builds the batch's message descriptors and weight offsets on the host
 //     (from the request lengths; no device scan, no copy of the payloads),
 //     then, with the lock released, issues one host-to-device copy, the
 //     persistent batched codec kernel that reads each payload where it lives
