@@ -373,11 +373,16 @@ def run_e2e(g, data, d: Dist):
 
     step(0)
     assert np.array_equal(dec_np[:GIB], data[:GIB])
-    # the host link's own rate right now (pinned torch copies of 1 GiB)
+    # the host link's own rate right now (pinned torch copies of 1 GiB), from
+    # and into each host buffer the round trip uses: the pages behind one
+    # pinned buffer have been seen to take device-to-host writes at a
+    # quarter of the rate of another's on the same box
     dbuf = torch.empty(GIB, dtype=torch.uint8, device="cuda")
     link = {}
     for name, fn in (("h2d", lambda: dbuf.copy_(h_src[:GIB], non_blocking=True)),
-                     ("d2h", lambda: h_dec[:GIB].copy_(dbuf, non_blocking=True))):
+                     ("d2h", lambda: h_dec[:GIB].copy_(dbuf, non_blocking=True)),
+                     ("h2d_from_encoded", lambda: dbuf.copy_(h_enc[:GIB], non_blocking=True)),
+                     ("d2h_into_encoded", lambda: h_enc[:GIB].copy_(dbuf, non_blocking=True))):
         fn()
         torch.cuda.synchronize()
         t = time.perf_counter()
