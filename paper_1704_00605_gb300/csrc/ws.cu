@@ -177,28 +177,36 @@ __global__ void __launch_bounds__(kWsThreads)
     k_ws_compact(const uint8_t* __restrict__ src, int64_t m, const int64_t* __restrict__ prefix,
                  uint8_t* __restrict__ out) {
   __shared__ __align__(16) uint8_t buf[kWsTile + 32];
+  // byte_perm selectors moving the kept bytes of a word (keep bits k4) to
+  // its low end, in order
+  __shared__ uint16_t sel[16];
+  if (threadIdx.x < 16) {
+    uint32_t v = 0, r = 0;
+    for (uint32_t k = 0; k < 4; ++k)
+      if (threadIdx.x & (1u << k)) v |= k << (4 * r++);
+    sel[threadIdx.x] = (uint16_t)v;
+  }
   const int64_t at = blockIdx.x * kWsTile + (int64_t)kWsPerThread * threadIdx.x;
   uint32_t w[16];
   const uint64_t mask = load_chars(src, m, at, w);
   int total;
-  const int local = block_excl_scan(__popcll(mask), &total);
+  const int local = block_excl_scan(__popcll(mask), &total);  // also orders sel
   uint8_t* d = out + prefix[blockIdx.x];
   const uintptr_t da = reinterpret_cast<uintptr_t>(d);
   const uint32_t o2 = (uint32_t)(da & 15u);
   uint32_t p = o2 + (uint32_t)local;
+  // branch-free, so that the lanes of a warp never split over a word with
+  // whitespace: the word's kept bytes moved down by one byte_perm, then
+  // stored under predicates
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const uint32_t k4 = (uint32_t)(mask >> (4 * i)) & 15u;
-    if (k4 == 15u) {  // the common case: four characters kept
-      buf[p] = (uint8_t)w[i];
-      buf[p + 1] = (uint8_t)(w[i] >> 8);
-      buf[p + 2] = (uint8_t)(w[i] >> 16);
-      buf[p + 3] = (uint8_t)(w[i] >> 24);
-      p += 4;
-    } else {
-      for (int k = 0; k < 4; ++k)
-        if (k4 & (1u << k)) buf[p++] = (uint8_t)(w[i] >> (8 * k));
-    }
+    const uint32_t v = __byte_perm(w[i], 0u, sel[k4]);
+    const uint32_t n = __popc(k4);
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (k < n) buf[p + k] = (uint8_t)(v >> (8 * k));
+    p += n;
   }
   fence_proxy_async_smem();
   __syncthreads();
