@@ -104,10 +104,11 @@ int b64_decode_host(const char *h_src, size_t m, uint8_t *h_dst, size_t *outlen,
  * entries, non-decreasing). The library writes out_off[0..nmsg] (device):
  * the exclusive prefix of b64_encoded_len (encode) or b64_decoded_cap
  * (decode) of the messages, and message j's output starts at dst +
- * out_off[j]. One persistent kernel codes every message: a device prefix sum
- * over per-message tile counts assigns fixed-size tiles, and per-message
- * padding and error positions are handled inside the kernel (Section 2's
- * rules per message). Asynchronous; per-message decode results go to
+ * out_off[j]. One persistent kernel codes every message: messages of up to
+ * 256 bytes / 344 characters one thread each, longer ones cut into
+ * fixed-size tiles that the warps share by bytes (a device prefix sum over
+ * the messages' weights), and per-message padding and error positions are
+ * handled inside the kernel (Section 2's rules per message). Asynchronous; per-message decode results go to
  * status[j], first_bad[j] (relative to the message start) and outlen[j].
  * dst must hold out_off[nmsg] bytes: call b64_batch_out_offsets first when
  * that total is not known. Temporary device memory is taken from the
