@@ -132,7 +132,9 @@ int b64_decode_batch(const char *src, const int64_t *in_off, int64_t nmsg, uint8
  * returns B64_ERR_ARG with nothing enqueued. Every call on a device shares
  * that array, so two calls that overlap on the GPU race: order them on one
  * stream or with events. The first call on a device looks up the array's
- * device address; make it before any stream capture. Asynchronous. */
+ * device address; make it before any stream capture. That address is kept
+ * until the process exits: resetting the device (cudaDeviceReset) between
+ * calls is not supported. Asynchronous. */
 int b64_decode_batch_noalloc(const char *src, const int64_t *in_off, int64_t nmsg, uint8_t *dst,
                              int64_t *out_off, int32_t *status, int64_t *first_bad,
                              int64_t *outlen, gb64_stream_t stream);
@@ -197,8 +199,10 @@ int b64_tune_load(const char *path);
  * of a batch's buffers come from one arena of memory_budget bytes allocated
  * at creation; a batch that does not fit waits for earlier outputs to be
  * released), forms a batch per free stream slot from the requests that have
- * arrived, packs their payloads with a gather kernel, runs the batched codec
- * kernels, and reports completions. Requests that arrive while batches run
+ * arrived, describes their payloads in place (one host-built descriptor per
+ * request: address, length, output offset; no gather and no copy of the
+ * payloads), runs the batched codec kernels on them, and reports
+ * completions. Requests that arrive while batches run
  * join the next batch; batches on different slots overlap on the GPU. */
 typedef struct b64_server b64_server;
 
@@ -312,6 +316,19 @@ const char *b64_last_error(void);
  * (B64_ERR_TIMEOUT) since the last query. Synchronizes the device. Returns 0,
  * B64_ERR_TIMEOUT or B64_ERR_CUDA. */
 int b64_device_fault(void);
+
+/* Test hook of the bounded waits (no counterpart in the paper). While
+ * stall != 0, every pipelined kernel launched afterwards (the TMA
+ * single-buffer encode and decode, and the batched kernels that stage tiles
+ * in shared memory) leaves out the first input copy of its first CTA (first
+ * warp, batched), so that CTA's wait on it runs out after wait_limit_ns
+ * (0 = the default of 2 s): the kernel records the fault word, waits
+ * (bounded) for its other copies in flight and returns, the call reports
+ * B64_ERR_TIMEOUT (decode results; b64_device_fault()), and no GPU fault,
+ * trap or hang is involved. stall = 0 restores normal operation, and
+ * wait_limit_ns then sets the limit of every bounded wait (0 = 2 s).
+ * Process-wide; for tests, not for concurrent use. Returns B64_OK. */
+int b64_test_stall_copies(int stall, uint64_t wait_limit_ns);
 
 #ifdef __cplusplus
 }

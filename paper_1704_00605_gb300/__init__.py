@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import importlib
 
-_SUBMODULES = ("build", "gb64", "workloads", "serve", "tune")
+_SUBMODULES = ("build", "gb64", "workloads")
 
 
 def load():

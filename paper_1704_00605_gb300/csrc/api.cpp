@@ -1,5 +1,6 @@
 // The C ABI of libgb64 (include/gb64.h): argument checks on the host, the
 // per-thread error text, device facts, and the single-buffer calls.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -93,6 +94,14 @@ const DeviceInfo* device_info(cudaError_t* err) {
   }
   return &d;
 }
+
+namespace {
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+std::atomic<uint64_t> g_wait_limit_ns{kDefaultWaitNs};
+std::atomic<uint32_t> g_stall{0};
+}  // namespace
+
+WaitTest wait_test() { return WaitTest{g_wait_limit_ns.load(), g_stall.load()}; }
 
 int read_and_clear_faults() {
   unsigned a = 0, b = 0;
@@ -271,6 +280,13 @@ const char* b64_status_str(int status) {
 }
 
 const char* b64_last_error(void) { return t_error.c_str(); }
+
+int b64_test_stall_copies(int stall, uint64_t wait_limit_ns) {
+  clear_error();
+  g_wait_limit_ns.store(wait_limit_ns ? wait_limit_ns : kDefaultWaitNs);
+  g_stall.store(stall ? 1u : 0u);
+  return B64_OK;
+}
 
 int b64_device_fault(void) {
   clear_error();

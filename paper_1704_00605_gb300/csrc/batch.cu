@@ -36,6 +36,7 @@ constexpr int kMaxBatchStages = 6;
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int64_t kScanPerBlock = (int64_t)kScanThreads * kScanItems;
+static_assert(kScanPerBlock == kBatchScanPerBlock, "batch_scratch_bytes sizes the scan blocks");
 constexpr int64_t kNoBad = INT64_MAX;
 constexpr int64_t kTileCost = kBatchTileCost;
 
@@ -912,7 +913,7 @@ template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
     k_batch_code(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ weight_off, TileShape ts,
                  uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
-                 uint32_t flags) {
+                 uint32_t flags, WaitTest wt) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t table[DECODE ? 256 : 64];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
@@ -946,9 +947,11 @@ __global__ void __launch_bounds__(NT)
     if (lane == 0) {
       walk_begin(walk, ms, weight_off, j0, w_begin, w_end, ts);
       TileView v;
+      // (test stall: the grid's first warp leaves out its first copy)
+      const bool stall = wt.stall && blockIdx.x == 0 && warp == 0;
       while (primed < S && walk_next(walk, ms, nmsg, ts, v)) {
         meta[warp][primed] = v;
-        issue_tile(v, wbase + primed * in_b, &full[warp][primed]);
+        if (!(stall && primed == 0)) issue_tile(v, wbase + primed * in_b, &full[warp][primed]);
         ++primed;
       }
       more = primed == S;
@@ -964,7 +967,7 @@ __global__ void __launch_bounds__(NT)
   uint32_t s = 0, phase = 0;
   while (pending > 0) {
     uint8_t* in = wbase + s * in_b;
-    const bool ok = mbar_wait_backoff(&full[warp][s], phase);
+    const bool ok = mbar_wait_backoff(&full[warp][s], phase, wt.limit_ns);
     if (__any_sync(0xFFFFFFFFu, !ok)) {
       timed_out = true;
       break;
@@ -1056,6 +1059,9 @@ __global__ void __launch_bounds__(NT)
 
 // Per-message status: first bad character wins, then the length rule, then
 // Appendix A's check (decoder of the final group returned a negative code).
+// While the fault word is set (a tile kernel gave up on a bounded wait, and
+// b64_device_fault has not cleared it since), every message reports
+// B64_ERR_TIMEOUT: some of them were never decoded.
 template <class Msgs>
 __global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restrict__ status,
                                       int64_t* __restrict__ first_bad,
@@ -1063,6 +1069,12 @@ __global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restri
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nmsg) return;
   const uint64_t m = (uint64_t)max((long long)0, (long long)msgs.len(j));
+  if (*(volatile unsigned int*)&g_batch_fault) {
+    status[j] = B64_ERR_TIMEOUT;
+    first_bad[j] = (int64_t)m;
+    outlen[j] = 0;
+    return;
+  }
   const uint64_t body_end = decode_body_end(m);
   const int64_t final = (body_end < m) ? outlen[j] : 0;
   const FinalStatus f = final_status(m, body_end, (unsigned long long)first_bad[j], final, flags);
@@ -1084,11 +1096,6 @@ __global__ void k_batch_decode_init(int64_t nmsg, int64_t* __restrict__ first_ba
 size_t batch_smem_bytes(int decode, const BatchConfig& c) {
   if (c.kernel == 2) return 0;  // unstaged tiles
   return (size_t)(c.threads / 32) * warp_smem_bytes(decode, c.tile, (uint32_t)c.stages);
-}
-
-size_t batch_scratch_bytes(int64_t nmsg) {
-  const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  return (size_t)(nmsg + 1) * 8 + (size_t)std::max<int64_t>(nparts, 1) * 16;
 }
 
 cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64_t* out_off,
@@ -1145,10 +1152,10 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
     }
   } else if (decode) {
     k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,
-                                                          first_bad, outlen, flags);
+                                                          first_bad, outlen, flags, wait_test());
   } else {
     k_batch_code<NT, 0, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,
-                                                          nullptr, nullptr, flags);
+                                                          nullptr, nullptr, flags, wait_test());
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !decode) return e;

@@ -61,9 +61,18 @@ cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uin
                               int64_t* outlen, const BatchConfig& cfg, bool init_results,
                               cudaStream_t stream, uint32_t flags = 0);
 
-// Bytes of scratch a batch of nmsg messages needs (weight_off and the
-// scan's block totals).
-size_t batch_scratch_bytes(int64_t nmsg);
+// Messages per block of the batch scan (its threads x items per thread).
+constexpr int64_t kBatchScanPerBlock = 512 * 4;
+
+// Bytes of scratch a batch of nmsg messages needs: weight_off (nmsg + 1
+// int64) and the scan's block totals (two int64 per scan block, at least one
+// block).
+constexpr size_t batch_scratch_bytes(int64_t nmsg) {
+  return (size_t)(nmsg + 1) * 8 +
+         (size_t)((nmsg + kBatchScanPerBlock - 1) / kBatchScanPerBlock > 0
+                      ? (nmsg + kBatchScanPerBlock - 1) / kBatchScanPerBlock
+                      : 1) * 16;
+}
 
 // Splits a scratch block of batch_scratch_bytes(nmsg) into its arrays.
 inline void batch_scratch_split(void* scratch, int64_t nmsg, int64_t** weight_off, void** parts) {

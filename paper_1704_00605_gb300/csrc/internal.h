@@ -65,6 +65,14 @@ size_t ws_scratch_bytes(uint64_t m);
 cudaError_t decode_ws_launch(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
                              void* scratch, uint32_t flags, cudaStream_t stream);
 
+// Limit of the pipelined kernels' bounded waits and the test stall of
+// b64_test_stall_copies (host state, passed to every launch).
+struct WaitTest {
+  uint64_t limit_ns;  // wait limit (default 2 s)
+  uint32_t stall;     // leave out the first copy of the first CTA / warp
+};
+WaitTest wait_test();
+
 // Reads and clears the fault words of every kernel file (current device).
 int read_and_clear_faults();
 int batch_read_and_clear_fault(unsigned int* out);

@@ -22,6 +22,8 @@
 //     call, so nothing left from the previous call needs clearing;
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress); make that first call before any stream capture.
+//     The address is kept for the life of the process, so the device must
+//     not be reset (cudaDeviceReset) between calls.
 #include <mutex>
 
 #include "batch.h"
@@ -33,6 +35,9 @@ namespace {
 
 constexpr int64_t kNoAllocMaxMsgs = 65536;
 constexpr size_t kNoAllocScratchBytes = 576u << 10;
+
+static_assert(batch_scratch_bytes(kNoAllocMaxMsgs) <= kNoAllocScratchBytes,
+              "the fixed scratch must hold a batch of the largest accepted size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 

@@ -46,6 +46,8 @@ struct EncArgs {
   uint32_t upt;
   uint32_t stages;
   uint32_t flags;
+  uint32_t stall;    // test: CTA 0 leaves out its first copy
+  uint64_t wait_ns;  // limit of the stage waits
 };
 
 struct DecArgs {
@@ -58,6 +60,8 @@ struct DecArgs {
   uint32_t stages;
   uint32_t flags;
   const uint64_t* m_dev;  // DEVLEN kernels: the length lives in device memory
+  uint32_t stall;         // test: CTA 0 leaves out its first copy
+  uint64_t wait_ns;       // limit of the stage waits
 };
 
 // ------------------------------------------------------------- encode/TMA
@@ -97,14 +101,14 @@ __global__ void __launch_bounds__(NT) k_encode_tma(EncArgs a) {
     fence_proxy_async_smem();
     for (uint32_t s = 0; s < S; ++s) {
       const uint64_t t = blockIdx.x + (uint64_t)s * gridDim.x;
-      if (t < ntiles) issue(t, s);
+      if (t < ntiles && !(a.stall && t == 0)) issue(t, s);
     }
   }
 
   uint32_t k = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const uint32_t s = k % S;
-    const bool ok = mbar_wait_bounded(&full[s], (k / S) & 1u);
+    const bool ok = mbar_wait_bounded(&full[s], (k / S) & 1u, a.wait_ns);
     const uint64_t off = t * tile_in;
     const uint32_t len = (uint32_t)tmin<uint64_t>(tile_in, a.n - off);
     const uint32_t nu = (len & ~15u) / 12u;
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a0) {
     fence_proxy_async_smem();
     for (uint32_t s = 0; s < S; ++s) {
       const uint64_t t = blockIdx.x + (uint64_t)s * gridDim.x;
-      if (t < ntiles) issue(t, s);
+      if (t < ntiles && !(a.stall && t == 0)) issue(t, s);
     }
   }
 
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a0) {
   uint32_t k = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const uint32_t s = k % S;
-    const bool ok = mbar_wait_bounded(&full[s], (k / S) & 1u);
+    const bool ok = mbar_wait_bounded(&full[s], (k / S) & 1u, a.wait_ns);
     const uint64_t off = t * tile_c;
     const uint32_t len = (uint32_t)tmin<uint64_t>(tile_c, a.m - off);
     const uint32_t body =
@@ -474,7 +478,8 @@ cudaError_t launch_encode_nt(const uint8_t* src, uint64_t n, uint8_t* dst, cudaS
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) &
                         15u) == 0;
   if (aligned) {
-    EncArgs a{src, n, dst, (uint32_t)cfg.upt, (uint32_t)cfg.stages, flags};
+    const WaitTest wt = wait_test();
+    EncArgs a{src, n, dst, (uint32_t)cfg.upt, (uint32_t)cfg.stages, flags, wt.stall, wt.limit_ns};
     const uint64_t tile_in = (uint64_t)NT * cfg.upt * 12u;
     const size_t smem = (size_t)cfg.stages * tile_in;
     const uint32_t f = flags & (kFlagUrl | kFlagNoPad);
@@ -505,6 +510,9 @@ cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileC
   DecArgs a = a0;
   a.upt = (uint32_t)cfg.upt;
   a.stages = (uint32_t)cfg.stages;
+  const WaitTest wt = wait_test();
+  a.stall = wt.stall;
+  a.wait_ns = wt.limit_ns;
   const bool aligned =
       ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15u) == 0;
   if (aligned) {
@@ -560,7 +568,7 @@ cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStre
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
                           b64_result* res, cudaStream_t stream, const TileConfig& cfg,
                           uint32_t flags) {
-  DecArgs a{src, m, body_end, dst, res, 0, 0, flags, nullptr};
+  DecArgs a{src, m, body_end, dst, res, 0, 0, flags, nullptr, 0, 0};
   return launch_decode_any_nt<false>(a, stream, cfg);
 }
 
@@ -568,7 +576,7 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uin
 cudaError_t launch_decode_devlen(const uint8_t* src, uint64_t m_max, const uint64_t* m_dev,
                                  uint8_t* dst, b64_result* res, cudaStream_t stream,
                                  const TileConfig& cfg, uint32_t flags) {
-  DecArgs a{src, m_max, decode_body_end(m_max), dst, res, 0, 0, flags, m_dev};
+  DecArgs a{src, m_max, decode_body_end(m_max), dst, res, 0, 0, flags, m_dev, 0, 0};
   return launch_decode_any_nt<true>(a, stream, cfg);
 }
 

@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "b64_status_str": (ctypes.c_char_p, [i32]),
         "b64_last_error": (ctypes.c_char_p, []),
         "b64_device_fault": (i32, []),
+        "b64_test_stall_copies": (i32, [i32, ctypes.c_uint64]),
         "b64_shape_get": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
         "b64_shape_set": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
         "b64_tune": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape), i32,
@@ -165,6 +166,12 @@ def b64_decoded_cap(m: int) -> int:
 
 def b64_device_fault() -> int:
     return int(lib().b64_device_fault())
+
+
+def b64_test_stall_copies(stall: bool, wait_limit_ns: int = 0) -> None:
+    """Test hook: while ``stall`` is set, pipelined kernels leave out the
+    first copy of their first CTA (warp) so its bounded wait runs out."""
+    lib().b64_test_stall_copies(1 if stall else 0, int(wait_limit_ns))
 
 
 # ------------------------------------------------------------ marshalling
