@@ -59,7 +59,9 @@ typedef struct {
   int64_t first_bad; /* as for b64_decode */
   int64_t outlen;    /* bytes written on B64_OK, else 0 */
   int32_t status;    /* a b64_status */
-  uint32_t internal; /* used by the library while the decode runs */
+  uint32_t internal; /* used by the library while the decode runs; afterwards
+                        it names the kernel path that finished the decode
+                        (an implementation detail, for tests) */
 } b64_result;
 
 /* Length of the encoding of n bytes: 4 * ceil(n / 3) (Section 2: three
@@ -145,7 +147,8 @@ enum {
   B64_KIND_ENCODE = 0,       /* b64_encode and the host-buffer encode */
   B64_KIND_DECODE = 1,       /* b64_decode(_async) and the host-buffer decode */
   B64_KIND_ENCODE_BATCH = 2, /* b64_encode_batch */
-  B64_KIND_DECODE_BATCH = 3  /* b64_decode_batch(_noalloc) */
+  B64_KIND_DECODE_BATCH = 3, /* b64_decode_batch(_noalloc) */
+  B64_KIND_DECODE_WS = 4     /* the one-pass line-model kernel of B64_FLAG_SKIP_WS */
 };
 
 /* A launch shape. Single kinds use threads, units_per_thread (12 input
@@ -161,7 +164,9 @@ enum {
  * unstaged), stages (staged input stages per warp, 2..6; 0 = 4) and
  * blocks_per_sm (0 = as many as fit); a staged shape's shared memory,
  * threads / 32 * (stages * (tile + 32) + (decode only) 3 * tile / 4 + 32)
- * bytes, must stay within 219 KiB. ms is a measured time. */
+ * bytes, must stay within 219 KiB. B64_KIND_DECODE_WS uses threads (256
+ * or 512), units_per_thread (16 kept characters each; a tile of up to 64 Ki
+ * characters) and stages (2..6). ms is a measured time. */
 typedef struct {
   int32_t threads;
   int32_t units_per_thread;
@@ -179,7 +184,7 @@ typedef struct {
 int b64_shape_get(int kind, int64_t total, int64_t nmsg, b64_shape *out);
 int b64_shape_set(int kind, int64_t total, int64_t nmsg, const b64_shape *shape);
 
-/* Autotune one bucket: generate `total` bytes (or characters) of random
+/* Autotune one bucket (the kinds 0-3): generate `total` bytes (or characters) of random
  * test data on the device (as nmsg messages for batch kinds), time every
  * candidate shape of the kind with CUDA events (median of 7 runs), and keep
  * the fastest for that bucket. Up to max_trials timed shapes are written to

@@ -104,12 +104,14 @@ std::atomic<uint32_t> g_stall{0};
 WaitTest wait_test() { return WaitTest{g_wait_limit_ns.load(), g_stall.load()}; }
 
 int read_and_clear_faults() {
-  unsigned a = 0, b = 0;
+  unsigned a = 0, b = 0, c = 0;
   int rc = single_read_and_clear_fault(&a);
   if (rc) return rc;
   rc = batch_read_and_clear_fault(&b);
   if (rc) return rc;
-  return (a | b) ? B64_ERR_TIMEOUT : B64_OK;
+  rc = ws_read_and_clear_fault(&c);
+  if (rc) return rc;
+  return (a | b | c) ? B64_ERR_TIMEOUT : B64_OK;
 }
 
 constexpr int kAllFlags = B64_FLAG_URL | B64_FLAG_NOPAD | B64_FLAG_STRICT_TAIL;

@@ -435,22 +435,20 @@ __device__ __forceinline__ void store12_warp(uint8_t* p, uint3 v, uint32_t lane,
 }
 
 // ------------------------------------------------------- final group
-// Final characters [body_end, m) of a message: a last quad that may end in
-// "=" or "==" (m % 4 == 0), or 1-3 characters of an incomplete group (an
-// unpadded final group under kFlagNoPad, else only validated). Lowers
-// *first_bad on an invalid character. Returns the bytes written (0..3), or
-// -(1 + k) when Appendix A's check (kFlagStrictTail) fails at character
-// body_end + k: with "==" (or 2 unpadded characters) the second character
-// must have (value * 16) mod 256 = 0, with "=" (or 3) the third must have
-// (value * 64) mod 256 = 0.
-static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t m, uint64_t body_end,
-                                            uint8_t* dst, const uint8_t* D,
-                                            unsigned long long* first_bad, uint32_t flags) {
-  const uint32_t cnt = (uint32_t)(m - body_end);
-  const uint8_t* p = src + body_end;
-  uint8_t* o = dst + body_end / 4 * 3;
+// The final characters p[0..cnt) of a message, cnt = 1..4: a last quad that
+// may end in "=" or "==" (quad: cnt == 4 and the message length is a
+// multiple of 4), or 1-3 characters of an incomplete group (an unpadded
+// final group under kFlagNoPad, else only validated). Writes the decoded
+// bytes at o. On an invalid character sets *bad to its index k (0..3) and
+// returns 0. Returns the bytes written (0..3), or -(1 + k) when Appendix A's
+// check (kFlagStrictTail) fails at character k: with "==" (or 2 unpadded
+// characters) the second character must have (value * 16) mod 256 = 0,
+// with "=" (or 3) the third must have (value * 64) mod 256 = 0.
+static __device__ __noinline__ int dec_final_chars(const uint8_t* p, uint32_t cnt, bool quad,
+                                                   uint8_t* o, const uint8_t* D, uint32_t* bad,
+                                                   uint32_t flags) {
   const bool strict = (flags & kFlagStrictTail) != 0;
-  if (cnt == 4 && m % 4 == 0) {
+  if (quad) {
     const uint32_t c[4] = {p[0], p[1], p[2], p[3]};
     uint32_t npad = 0;
     if (c[3] == kPadChar) npad = (c[2] == kPadChar) ? 2 : 1;
@@ -459,7 +457,7 @@ static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t 
       const bool is_pad = k >= 4 - npad;
       const uint32_t d = D[c[k]];
       if (!is_pad && (d & kBadFlag)) {
-        atomicMin(first_bad, (unsigned long long)(body_end + k));
+        *bad = k;
         return 0;
       }
       v[k] = is_pad ? 0u : d;
@@ -476,7 +474,7 @@ static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t 
   for (uint32_t k = 0; k < cnt; ++k) {
     const uint32_t d = D[p[k]];
     if (d & kBadFlag) {
-      atomicMin(first_bad, (unsigned long long)(body_end + k));
+      *bad = k;
       return 0;
     }
     if (k < 3) v[k] = d;
@@ -487,6 +485,24 @@ static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t 
   o[0] = (uint8_t)((v[0] << 2) | (v[1] >> 4));
   if (cnt == 3) o[1] = (uint8_t)(((v[1] & 15u) << 4) | (v[2] >> 2));
   return (int)cnt - 1;
+}
+
+// Final characters [body_end, m) of a message read from src (see
+// dec_final_chars); lowers *first_bad on an invalid character. Returns the
+// bytes written (0..3), or -(1 + k) when Appendix A's check fails at
+// character body_end + k.
+static __device__ __noinline__ int dec_final_group(const uint8_t* src, uint64_t m, uint64_t body_end,
+                                            uint8_t* dst, const uint8_t* D,
+                                            unsigned long long* first_bad, uint32_t flags) {
+  const uint32_t cnt = (uint32_t)(m - body_end);
+  uint32_t bad = ~0u;
+  const int r = dec_final_chars(src + body_end, cnt, cnt == 4 && m % 4 == 0,
+                                dst + body_end / 4 * 3, D, &bad, flags);
+  if (bad != ~0u) {
+    atomicMin(first_bad, (unsigned long long)(body_end + bad));
+    return 0;
+  }
+  return r;
 }
 
 // ------------------------------------------------------ error reduction

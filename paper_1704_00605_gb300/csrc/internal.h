@@ -77,5 +77,6 @@ WaitTest wait_test();
 int read_and_clear_faults();
 int batch_read_and_clear_fault(unsigned int* out);
 int single_read_and_clear_fault(unsigned int* out);
+int ws_read_and_clear_fault(unsigned int* out);
 
 }  // namespace gb64

@@ -59,9 +59,8 @@ struct DecArgs {
   uint32_t upt;
   uint32_t stages;
   uint32_t flags;
-  const uint64_t* m_dev;  // DEVLEN kernels: the length lives in device memory
-  uint32_t stall;         // test: CTA 0 leaves out its first copy
-  uint64_t wait_ns;       // limit of the stage waits
+  uint32_t stall;     // test: CTA 0 leaves out its first copy
+  uint64_t wait_ns;  // limit of the stage waits
 };
 
 // ------------------------------------------------------------- encode/TMA
@@ -227,15 +226,8 @@ __device__ void dec_finish(const DecArgs& a, bool timed_out) {
 }
 
 // ------------------------------------------------------------- decode/TMA
-// DEVLEN: m is read from a.m_dev at kernel start (the grid was sized for
-// the host-side bound a.m); the default instantiation has no such code.
-template <int NT, bool DEVLEN>
-__global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a0) {
-  DecArgs a = a0;
-  if (DEVLEN) {
-    a.m = *a0.m_dev;
-    a.body_end = decode_body_end(a.m);
-  }
+template <int NT>
+__global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint8_t D[256];
   __shared__ __align__(8) uint64_t full[kMaxStages];
@@ -353,13 +345,8 @@ __global__ void __launch_bounds__(NT) k_decode_tma(DecArgs a0) {
 }
 
 // --------------------------------------------------------- decode/generic
-template <int NT, bool DEVLEN>
-__global__ void __launch_bounds__(NT) k_decode_any(DecArgs a0) {
-  DecArgs a = a0;
-  if (DEVLEN) {
-    a.m = *a0.m_dev;
-    a.body_end = decode_body_end(a.m);
-  }
+template <int NT>
+__global__ void __launch_bounds__(NT) k_decode_any(DecArgs a) {
   __shared__ uint8_t D[256];
   init_tables(nullptr, D, a.flags & kFlagUrl);
   unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(&a.res->first_bad);
@@ -504,7 +491,7 @@ cudaError_t launch_encode_nt(const uint8_t* src, uint64_t n, uint8_t* dst, cudaS
   return cudaGetLastError();
 }
 
-template <int NT, bool DEVLEN>
+template <int NT>
 cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileConfig& cfg,
                              const DeviceInfo* di) {
   DecArgs a = a0;
@@ -521,32 +508,31 @@ cudaError_t launch_decode_nt(const DecArgs& a0, cudaStream_t stream, const TileC
     const size_t smem = (size_t)cfg.stages * tile_c + 2 * tile_o;
     int bps = 0;
     cudaError_t e =
-        kernel_prepare(reinterpret_cast<const void*>(k_decode_tma<NT, DEVLEN>), smem, NT, &bps);
+        kernel_prepare(reinterpret_cast<const void*>(k_decode_tma<NT>), smem, NT, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const uint64_t ntiles = std::max<uint64_t>(1, (a.m + tile_c - 1) / tile_c);
     const int grid =
         (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * resident_ctas(bps, cfg));
-    k_decode_tma<NT, DEVLEN><<<grid, NT, smem, stream>>>(a);
+    k_decode_tma<NT><<<grid, NT, smem, stream>>>(a);
     return cudaGetLastError();
   }
   const uint64_t units = a.m / 16 + 1;
   const int grid =
       (int)std::max<uint64_t>(1, std::min<uint64_t>((units + NT - 1) / NT, (uint64_t)di->sm_count * 8));
-  k_decode_any<NT, DEVLEN><<<grid, NT, 0, stream>>>(a);
+  k_decode_any<NT><<<grid, NT, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
-template <bool DEVLEN>
 cudaError_t launch_decode_any_nt(const DecArgs& a, cudaStream_t stream, const TileConfig& cfg) {
   if (!valid_config(cfg)) return cudaErrorInvalidValue;
   cudaError_t e;
   const DeviceInfo* di = device_info(&e);
   if (!di) return e;
   switch (cfg.threads) {
-    case 128: return launch_decode_nt<128, DEVLEN>(a, stream, cfg, di);
-    case 512: return launch_decode_nt<512, DEVLEN>(a, stream, cfg, di);
-    default: return launch_decode_nt<256, DEVLEN>(a, stream, cfg, di);
+    case 128: return launch_decode_nt<128>(a, stream, cfg, di);
+    case 512: return launch_decode_nt<512>(a, stream, cfg, di);
+    default: return launch_decode_nt<256>(a, stream, cfg, di);
   }
 }
 
@@ -568,16 +554,8 @@ cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, cudaStre
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uint8_t* dst,
                           b64_result* res, cudaStream_t stream, const TileConfig& cfg,
                           uint32_t flags) {
-  DecArgs a{src, m, body_end, dst, res, 0, 0, flags, nullptr, 0, 0};
-  return launch_decode_any_nt<false>(a, stream, cfg);
-}
-
-// Decode of a whole message whose length is at *m_dev (at most m_max).
-cudaError_t launch_decode_devlen(const uint8_t* src, uint64_t m_max, const uint64_t* m_dev,
-                                 uint8_t* dst, b64_result* res, cudaStream_t stream,
-                                 const TileConfig& cfg, uint32_t flags) {
-  DecArgs a{src, m_max, decode_body_end(m_max), dst, res, 0, 0, flags, m_dev, 0, 0};
-  return launch_decode_any_nt<true>(a, stream, cfg);
+  DecArgs a{src, m, body_end, dst, res, 0, 0, flags, 0, 0};
+  return launch_decode_any_nt(a, stream, cfg);
 }
 
 int single_read_and_clear_fault(unsigned int* out) {

@@ -65,6 +65,8 @@ BatchConfig batch_config_of(const b64_shape& s) {
 }
 
 bool shape_valid(int kind, const b64_shape& s) {
+  if (kind == kDecodeWs)
+    return ws_lines_config_valid(TileConfig{s.threads, s.units_per_thread, s.stages, 0});
   if (kind == kSingleEncode || kind == kSingleDecode) {
     TileConfig c{s.threads, s.units_per_thread, s.stages, s.blocks_per_sm};
     return (c.threads == 128 || c.threads == 256 || c.threads == 512) && c.upt >= 1 &&
@@ -161,7 +163,7 @@ std::vector<b64_shape> batch_candidates(int decode) {
 }  // namespace
 
 int bucket_of(int kind, int64_t total, int64_t nmsg) {
-  if (kind == kSingleEncode || kind == kSingleDecode) {
+  if (kind == kSingleEncode || kind == kSingleDecode || kind == kDecodeWs) {
     const int64_t n = total < 0 ? 0 : total;
     if (n < (1ll << 16)) return 0;
     if (n < (1ll << 20)) return 1;
@@ -189,6 +191,14 @@ TileConfig single_config(int decode, uint64_t n) {
   return decode ? default_decode_config(n) : default_encode_config(n);
 }
 
+TileConfig ws_lines_config(uint64_t m) {
+  std::lock_guard<std::mutex> g(g_mu);
+  load_env_once_locked();
+  const Entry& e = g_table[kDecodeWs][bucket_of(kDecodeWs, (int64_t)m, 1)];
+  if (e.set) return TileConfig{e.s.threads, e.s.units_per_thread, e.s.stages, 0};
+  return default_ws_lines_config(m);
+}
+
 BatchConfig tuned_batch_config(int decode, int64_t nmsg, int64_t total_bytes) {
   std::lock_guard<std::mutex> g(g_mu);
   load_env_once_locked();
@@ -210,7 +220,10 @@ int b64_shape_get(int kind, int64_t total, int64_t nmsg, b64_shape* out) {
     set_error("bad kind or null output");
     return B64_ERR_ARG;
   }
-  if (kind == kSingleEncode || kind == kSingleDecode) {
+  if (kind == kDecodeWs) {
+    const TileConfig c = ws_lines_config((uint64_t)std::max<int64_t>(total, 0));
+    *out = b64_shape{c.threads, c.upt, c.stages, 0, (int64_t)c.threads * c.upt * 16, 0.f};
+  } else if (kind == kSingleEncode || kind == kSingleDecode) {
     const TileConfig c = single_config(kind == kSingleDecode, (uint64_t)std::max<int64_t>(total, 0));
     const int unit = kind == kSingleDecode ? 16 : 12;
     *out = b64_shape{c.threads, c.upt, c.stages, c.blocks_per_sm,
@@ -232,14 +245,15 @@ int b64_shape_set(int kind, int64_t total, int64_t nmsg, const b64_shape* s) {
     set_error("shape not valid for this kind");
     return B64_ERR_ARG;
   }
-  if (kind == kSingleEncode || kind == kSingleDecode) {
+  if (kind == kSingleEncode || kind == kSingleDecode || kind == kDecodeWs) {
     // with a device present, the shape must fit its shared memory
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
       cudaError_t e;
       const DeviceInfo* di = device_info(&e);
       const TileConfig c{s->threads, s->units_per_thread, s->stages, s->blocks_per_sm};
-      const size_t need = single_smem_bytes(kind == kSingleDecode, c);
+      const size_t need = kind == kDecodeWs ? ws_lines_smem_bytes(c)
+                                            : single_smem_bytes(kind == kSingleDecode, c);
       if (di && need + 1024 > (size_t)di->max_smem_optin) {
         set_error("shape needs %zu bytes of shared memory per CTA; the device allows %d", need,
                   di->max_smem_optin);
@@ -293,6 +307,10 @@ int b64_tune(int kind, int64_t total, int64_t nmsg, b64_shape* trials, int max_t
   if (kind < 0 || kind >= kKinds || total <= 0 ||
       ((kind == kBatchEncode || kind == kBatchDecode) && (nmsg <= 0 || nmsg > total))) {
     set_error("bad kind, size or message count");
+    return B64_ERR_ARG;
+  }
+  if (kind == kDecodeWs) {
+    set_error("the line-model kernel's shape is set with b64_shape_set, not tuned");
     return B64_ERR_ARG;
   }
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);

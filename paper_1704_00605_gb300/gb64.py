@@ -35,6 +35,7 @@ B64_KIND_ENCODE = 0
 B64_KIND_DECODE = 1
 B64_KIND_ENCODE_BATCH = 2
 B64_KIND_DECODE_BATCH = 3
+B64_KIND_DECODE_WS = 4
 
 
 class b64_server_config(ctypes.Structure):
