@@ -324,9 +324,10 @@ int b64_device_fault(void);
 
 /* Test hook of the bounded waits (no counterpart in the paper). While
  * stall != 0, every pipelined kernel launched afterwards (the TMA
- * single-buffer encode and decode, and the batched kernels that stage tiles
- * in shared memory) leaves out the first input copy of its first CTA (first
- * warp, batched), so that CTA's wait on it runs out after wait_limit_ns
+ * single-buffer encode and decode, the whitespace decode's line kernel, and
+ * the batched kernel that stages tiles in shared memory) leaves out the
+ * first input copy of its first CTA (of the first warp, batched), so that
+ * the wait on it runs out after wait_limit_ns
  * (0 = the default of 2 s): the kernel records the fault word, waits
  * (bounded) for its other copies in flight and returns, the call reports
  * B64_ERR_TIMEOUT (decode results; b64_device_fault()), and no GPU fault,
