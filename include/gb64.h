@@ -289,9 +289,14 @@ void b64_server_destroy(b64_server *server);
 /*   B64_FLAG_SKIP_WS      decode only, single buffer: space, line feed and
  *                         carriage return are removed before decoding
  *                         (Appendix B); first_bad is an index into the
- *                         original input, outlen counts decoded bytes. Takes
- *                         scratch of about m bytes from the stream-ordered
- *                         allocator. Not accepted by encode or batches. */
+ *                         original input, outlen counts decoded bytes. Uses
+ *                         a scratch buffer of about m bytes that the library
+ *                         keeps per device between calls (grown as needed,
+ *                         freed by b64_release_scratch); calls on different
+ *                         streams that use it run one after the other. While
+ *                         the stream captures a graph the scratch comes from
+ *                         the stream-ordered allocator instead. Not accepted
+ *                         by encode or batches. */
 #define B64_FLAG_SKIP_WS 8
 
 size_t b64_encoded_len_ex(size_t n, int flags);
@@ -321,6 +326,12 @@ const char *b64_last_error(void);
  * (B64_ERR_TIMEOUT) since the last query. Synchronizes the device. Returns 0,
  * B64_ERR_TIMEOUT or B64_ERR_CUDA. */
 int b64_device_fault(void);
+
+/* Frees the scratch buffer that the B64_FLAG_SKIP_WS decode keeps on the
+ * current device, after the last call that uses it has finished (waits for
+ * it); the next such call allocates it again. Returns B64_OK or
+ * B64_ERR_CUDA. */
+int b64_release_scratch(void);
 
 /* Test hook of the bounded waits (no counterpart in the paper). While
  * stall != 0, every pipelined kernel launched afterwards (the TMA

@@ -149,13 +149,8 @@ int decode_enqueue(const char* src, size_t m, uint8_t* dst, b64_result* d_result
   if (e != cudaSuccess) return cuda_status(e, "decode: clearing the result");
   if (flags & B64_FLAG_SKIP_WS) {
     if (m == 0) return decode_enqueue(src, m, dst, d_result, stream, flags & ~B64_FLAG_SKIP_WS);
-    void* scratch = nullptr;
-    e = cudaMallocAsync(&scratch, ws_scratch_bytes(m), stream);
-    if (e != cudaSuccess) return cuda_status(e, "decode: whitespace scratch");
-    e = decode_ws_launch(reinterpret_cast<const uint8_t*>(src), m, dst, d_result, scratch,
-                         (uint32_t)flags, stream);
-    const cudaError_t ef = cudaFreeAsync(scratch, stream);
-    if (e == cudaSuccess) e = ef;
+    e = decode_ws_enqueue(reinterpret_cast<const uint8_t*>(src), m, dst, d_result,
+                          (uint32_t)flags, stream);
     if (e != cudaSuccess) return cuda_status(e, "decode: whitespace launch");
     return B64_OK;
   }
@@ -295,6 +290,13 @@ int b64_device_fault(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e, "device fault query");
   return read_and_clear_faults();
+}
+
+int b64_release_scratch(void) {
+  clear_error();
+  const cudaError_t e = ws_release_scratch();
+  if (e != cudaSuccess) return cuda_status(e, "releasing the whitespace scratch");
+  return B64_OK;
 }
 
 }  // extern "C"

@@ -232,13 +232,17 @@ __device__ __forceinline__ uint32_t enc_tail_group(uint32_t b0, uint32_t b1, uin
 // --------------------------------------------------------------- decode
 // One quad of Algorithm 2's main loop: four characters (little-endian word)
 // -> 24-bit value a*2^18 + b*2^12 + c*2^6 + d; err collects the table flags.
+// Each character is picked out by one byte_perm, and the value is built by
+// multiply-adds (the same value as shifts and ors for entries below 64; any
+// other entry is flagged), which leaves the integer ALU pipe, the busiest in
+// the decoders, fewer instructions.
 __device__ __forceinline__ uint32_t dec_quad(uint32_t x, const uint8_t* D, uint32_t& err) {
-  const uint32_t a = D[x & 0xFFu];
-  const uint32_t b = D[(x >> 8) & 0xFFu];
-  const uint32_t c = D[(x >> 16) & 0xFFu];
+  const uint32_t a = D[__byte_perm(x, 0u, 0x4440)];
+  const uint32_t b = D[__byte_perm(x, 0u, 0x4441)];
+  const uint32_t c = D[__byte_perm(x, 0u, 0x4442)];
   const uint32_t d = D[x >> 24];
   err |= a | b | c | d;
-  return (((((a << 6) | b) << 6) | c) << 6) | d;
+  return ((a * 64u + b) * 64u + c) * 64u + d;
 }
 
 // Four quads (16 characters) -> 12 output bytes (three little-endian words).

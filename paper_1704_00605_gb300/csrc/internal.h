@@ -59,11 +59,12 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint64_t body_end, uin
                           b64_result* res, cudaStream_t stream, const TileConfig& cfg,
                           uint32_t flags = 0);
 
-// Whitespace-removing decode (ws.cu): scratch bytes for m characters, and
-// the launch (counts, scan, compaction, decode, mapping of first_bad).
-size_t ws_scratch_bytes(uint64_t m);
-cudaError_t decode_ws_launch(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
-                             void* scratch, uint32_t flags, cudaStream_t stream);
+// Whitespace-removing decode (ws.cu): the launch into the device's kept
+// scratch (or, under graph capture, a stream-ordered allocation), and the
+// release of that scratch (waits for its last user).
+cudaError_t decode_ws_enqueue(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
+                              uint32_t flags, cudaStream_t stream);
+cudaError_t ws_release_scratch();
 
 // Limit of the pipelined kernels' bounded waits and the test stall of
 // b64_test_stall_copies (host state, passed to every launch).

@@ -16,25 +16,31 @@
 // masks otherwise; with no line breaks and an aligned input the window is
 // one 16-byte load). The model is checked on every byte of the input: a kept
 // position must not hold whitespace (the decode table flags it), a
-// separator position must. If any byte breaks the model, the kernel leaves
-// the result untouched and raises a flag on which the general path below
-// runs instead; so the result is always that of the general path.
+// separator position must (one short pass per tile over the separators of
+// its lines). The kernel is one cooperative launch: after their tiles the
+// CTAs meet at a grid barrier, and if any byte broke the model they clear
+// the result and decode the input again by the general path below, in the
+// same launch; so the result is always that of the general path.
 //
-// General path (any whitespace), one cooperative kernel (k_ws_general) that
-// returns at once unless the flag is set; its phases, between grid barriers:
-//   1. per tile of kWsTile characters (64 per thread), the number kept;
-//      whitespace is found four bytes at a time;
-//   2. the exclusive prefix of the tile counts (CTA 0); its last entry is
-//      the compacted length m';
-//   3. every tile's kept characters packed at its prefix (a block scan of
-//      the per-thread counts) in shared memory and written to a scratch
-//      buffer with one bulk store;
+// General path (any whitespace; also when the input has no usable line
+// model or the output is not 16-byte aligned), over warp tiles of 2048
+// characters (64 per lane) that each warp works on alone, its phases
+// between grid barriers:
+//   1. per warp tile, the number kept; whitespace is found four bytes at a
+//      time;
+//   2. the exclusive prefix of the counts (each CTA sums a range, then
+//      scans it from the sum of the ranges before it); its last entry is the
+//      compacted length m';
+//   3. every warp tile's kept characters packed at its prefix (a warp scan
+//      of the lane counts) in the warp's shared buffer and written to a
+//      scratch buffer with one bulk store;
 //   4. the packed characters decoded (Algorithm 2), the first bad index
 //      reduced in compacted offsets;
 //   5. the status, first_bad mapped back to an original offset (binary
-//      search over the tile prefix, then a warp scan inside the tile); on
+//      search over the prefix, then a warp scan inside the warp tile); on
 //      success first_bad = m.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -43,14 +49,13 @@
 namespace gb64 {
 namespace {
 
-constexpr int kWsThreads = 256;
-constexpr int kWsPerThread = 64;                          // characters per thread
-constexpr int64_t kWsTile = kWsThreads * kWsPerThread;  // characters per tile
+constexpr int kWsPerThread = 64;                    // characters per lane in a warp tile
+constexpr int64_t kWarpTile = 32 * kWsPerThread;  // characters per warp tile of the general path
+constexpr int kMaxWsCtas = 1024;                    // bound of the per-CTA totals in the scratch
 
-// Flags shared by the line-model kernel, the general path and the host; at
-// the start of the scratch block (cleared, or use_general set, by the host).
+// Flags shared by the CTAs of a launch; at the start of the scratch block
+// (cleared by the host before each launch).
 struct WsHeader {
-  uint32_t use_general;  // non-zero: the general path decodes
   uint32_t violation;    // some byte broke the line model
   uint32_t bar_count;    // grid barrier of the general path: CTAs arrived,
   uint32_t bar_gen;      // and the barrier's generation
@@ -71,9 +76,9 @@ __device__ __forceinline__ uint32_t keep4(uint32_t w) {
 }
 
 // The 64 characters [at, at + 64) a thread owns, as 16 words (characters
-// past m read as space), and their keep-mask (bit k = character k kept).
-__device__ __forceinline__ uint64_t load_chars(const uint8_t* src, int64_t m, int64_t at,
-                                               uint32_t* w) {
+// past m read as space).
+__device__ __forceinline__ void load_chars(const uint8_t* src, int64_t m, int64_t at,
+                                           uint32_t (&w)[16]) {
   if (m - at >= kWsPerThread) {
     uint4 v[4];
 #pragma unroll
@@ -96,43 +101,34 @@ __device__ __forceinline__ uint64_t load_chars(const uint8_t* src, int64_t m, in
       w[i] = x;
     }
   }
+}
+
+// Keep-mask of 64 characters (bit k = character k kept).
+__device__ __forceinline__ uint64_t keep_mask(const uint32_t (&w)[16]) {
   uint64_t mask = 0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) mask |= (uint64_t)keep4(w[i]) << (4 * i);
   return mask;
 }
 
-// Block-wide exclusive scan of one int per thread (kWsThreads threads).
-__device__ __forceinline__ int block_excl_scan(int v, int* total) {
-  __shared__ int warp_sums[kWsThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
+// The lane's 64 characters of a warp tile, loaded one step ahead: next
+// holds those of warp tile t (loaded by the previous step); they move to cur
+// and the warp's next tile (t + stride) is loaded into next, so that its
+// loads are in flight while tile t is worked on.
+__device__ __forceinline__ void step_chars(const uint8_t* src, int64_t m, int64_t t,
+                                           int64_t stride, int64_t ntiles, uint32_t (&cur)[16],
+                                           uint32_t (&next)[16]) {
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int s = lane < kWsThreads / 32 ? warp_sums[lane] : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, s, d);
-      if (lane >= d) s += y;
-    }
-    if (lane < kWsThreads / 32) warp_sums[lane] = s;
-  }
-  __syncthreads();
-  *total = warp_sums[kWsThreads / 32 - 1];
-  const int r = (warp ? warp_sums[warp - 1] : 0) + x - v;
-  __syncthreads();
-  return r;
+  for (int i = 0; i < 16; ++i) cur[i] = next[i];
+  const int64_t tn = t + stride;
+  if (tn < ntiles) load_chars(src, m, tn * kWarpTile + (int64_t)kWsPerThread * (threadIdx.x & 31u), next);
 }
 
-// Block-wide exclusive scan of one int64 per thread (kWsThreads threads).
+// Block-wide exclusive scan of one int64 per thread (NT threads); *total
+// gets the sum.
+template <int NT>
 __device__ __forceinline__ int64_t block_excl_scan64(int64_t v, int64_t* total) {
-  __shared__ int64_t warp_sums64[kWsThreads / 32];
+  __shared__ int64_t warp_sums64[NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t x = v;
 #pragma unroll
@@ -143,87 +139,91 @@ __device__ __forceinline__ int64_t block_excl_scan64(int64_t v, int64_t* total) 
   if (lane == 31) warp_sums64[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    int64_t t = lane < kWsThreads / 32 ? warp_sums64[lane] : 0;
+    int64_t t = lane < NT / 32 ? warp_sums64[lane] : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int64_t y = __shfl_up_sync(0xFFFFFFFFu, t, d);
       if (lane >= d) t += y;
     }
-    if (lane < kWsThreads / 32) warp_sums64[lane] = t;
+    if (lane < NT / 32) warp_sums64[lane] = t;
   }
   __syncthreads();
-  *total = warp_sums64[kWsThreads / 32 - 1];
+  *total = warp_sums64[NT / 32 - 1];
   const int64_t r = (warp ? warp_sums64[warp - 1] : 0) + x - v;
   __syncthreads();
   return r;
 }
 
-// Kept characters of one tile (block-wide).
-__device__ __forceinline__ int count_tile(const uint8_t* src, int64_t m, int64_t tile) {
-  const int64_t at = tile * kWsTile + (int64_t)kWsPerThread * threadIdx.x;
-  uint32_t w[16];
-  const int c = __popcll(load_chars(src, m, at, w));
-  int total;
-  block_excl_scan(c, &total);
+// Block-wide sum of one int64 per thread (NT threads).
+template <int NT>
+__device__ __forceinline__ int64_t block_sum64(int64_t v) {
+  int64_t total;
+  block_excl_scan64<NT>(v, &total);
   return total;
 }
 
-// Packs one tile's kept characters (block-wide) at out + its prefix: in
-// shared memory at the output's phase (position o2 + i holds output byte i,
-// o2 = the output address mod 16), then the aligned interior by one bulk
-// store, the ragged ends (at most 15 bytes each) by byte stores. buf holds
-// kWsTile + 32 bytes; sel the 16 byte_perm selectors that move the kept
-// bytes of a word (keep bits k4) to its low end, in order.
-__device__ __forceinline__ void compact_tile(const uint8_t* src, int64_t m, int64_t tile,
-                                             int64_t prefix, uint8_t* out, uint8_t* buf,
-                                             const uint16_t* sel) {
-  const int64_t at = tile * kWsTile + (int64_t)kWsPerThread * threadIdx.x;
-  uint32_t w[16];
-  const uint64_t mask = load_chars(src, m, at, w);
-  int total;
-  const int local = block_excl_scan(__popcll(mask), &total);  // also orders buf's reuse
-  uint8_t* d = out + prefix;
+// Packs one warp tile's kept characters (the lane's 64 in w) at out +
+// offset, by the warp alone: in its shared buffer wbuf (kWarpTile + 32
+// bytes) at the output's phase (position o2 + i holds output byte i, o2 =
+// the output address mod 16), then the aligned interior by one bulk store,
+// the ragged ends (at most 15 bytes each) by byte stores of lanes 0..15 and
+// 16..31. sel: the 16 byte_perm selectors that move the kept bytes of a word
+// (keep bits k4) to its low end, in order. The bulk store of the previous
+// tile has finished reading wbuf before it is written again.
+__device__ __forceinline__ void compact_warp_tile(const uint32_t (&w)[16], int64_t offset,
+                                                  uint8_t* out, uint8_t* wbuf,
+                                                  const uint16_t* sel) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t mask = keep_mask(w);
+  const uint32_t n = (uint32_t)__popcll(mask);
+  uint32_t incl = n;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if ((int)lane >= d) incl += y;
+  }
+  const uint32_t olen = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  uint8_t* d = out + offset;
   const uintptr_t da = reinterpret_cast<uintptr_t>(d);
   const uint32_t o2 = (uint32_t)(da & 15u);
-  uint32_t p = o2 + (uint32_t)local;
-  // branch-free, so that the lanes of a warp never split over a word with
-  // whitespace: the word's kept bytes moved down by one byte_perm, then
-  // stored under predicates
+  if (lane == 0) bulk_wait_read_all();
+  __syncwarp();
+  uint32_t p = o2 + incl - n;
+  // branch-free, so that the lanes never split over a word with whitespace:
+  // the word's kept bytes moved down by one byte_perm, then stored under
+  // predicates
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const uint32_t k4 = (uint32_t)(mask >> (4 * i)) & 15u;
     const uint32_t v = __byte_perm(w[i], 0u, sel[k4]);
-    const uint32_t n = __popc(k4);
+    const uint32_t c = __popc(k4);
 #pragma unroll
     for (uint32_t k = 0; k < 4; ++k)
-      if (k < n) buf[p + k] = (uint8_t)(v >> (8 * k));
-    p += n;
+      if (k < c) wbuf[p + k] = (uint8_t)(v >> (8 * k));
+    p += c;
   }
   fence_proxy_async_smem();
-  __syncthreads();
-  const uint32_t olen = (uint32_t)total;
+  __syncwarp();
   const uintptr_t lo = (da + 15u) & ~(uintptr_t)15u, hi = (da + olen) & ~(uintptr_t)15u;
-  if (threadIdx.x == 0 && hi > lo) {
-    tma_store_1d(reinterpret_cast<void*>(lo), buf + (o2 ? 16u : 0u), (uint32_t)(hi - lo));
+  if (lane == 0 && hi > lo) {
+    tma_store_1d(reinterpret_cast<void*>(lo), wbuf + (o2 ? 16u : 0u), (uint32_t)(hi - lo));
     bulk_commit();
   }
   const uint32_t head = (uint32_t)(tmin<uintptr_t>(lo, da + olen) - da);
   const uint32_t ie = hi > lo ? (uint32_t)(hi - da) : head;
-  const uint32_t t = threadIdx.x;
-  if (t < head) {
-    d[t] = buf[o2 + t];
-  } else if (t >= 32u && t - 32u < olen - ie) {
-    d[ie + t - 32u] = buf[o2 + ie + t - 32u];
+  if (lane < head) {
+    d[lane] = wbuf[o2 + lane];
+  } else if (lane >= 16u && lane - 16u < olen - ie) {
+    d[ie + lane - 16u] = wbuf[o2 + ie + lane - 16u];
   }
-  if (threadIdx.x == 0) bulk_wait_read_all();  // buf is free for the next tile
-  __syncthreads();
+  __syncwarp();
 }
 
 __device__ __forceinline__ bool is_ws(uint32_t x) { return x == 0x20 || x == 0x0A || x == 0x0D; }
 
 // Original index of compacted character k (k < prefix[ntiles]), by one
-// warp: the tile holding it (binary search of the tile prefix), then the
-// kept characters of each lane's 1/32 of the tile counted and prefixed, then
+// warp: the warp tile holding it (binary search of the prefix), then the
+// kept characters of each lane's 64 of the tile counted and prefixed, then
 // one lane's scan of its part.
 __device__ int64_t original_index(const uint8_t* src, int64_t m, const int64_t* prefix,
                                   int64_t ntiles, int64_t k, uint32_t lane) {
@@ -232,8 +232,8 @@ __device__ int64_t original_index(const uint8_t* src, int64_t m, const int64_t* 
     const int64_t mid = (lo + hi) / 2;
     if (prefix[mid] <= k) lo = mid; else hi = mid;
   }
-  const int64_t part = kWsTile / 32;
-  const int64_t b = lo * kWsTile + lane * part, e = tmin<int64_t>(m, b + part);
+  const int64_t part = kWsPerThread;
+  const int64_t b = lo * kWarpTile + lane * part, e = tmin<int64_t>(m, b + part);
   int c = 0;
   for (int64_t i = b; i < e; ++i) c += !is_ws(src[i]);
   int incl = c;
@@ -289,92 +289,129 @@ __device__ bool grid_sync(WsHeader* h, uint64_t limit_ns) {
   return __syncthreads_and(ok) != 0;
 }
 
+// The status of a call whose grid barrier gave up (thread 0 of each CTA
+// that saw it; the same values from each).
+__device__ __forceinline__ void ws_timed_out(b64_result* res, uint64_t m) {
+  if (threadIdx.x != 0) return;
+  volatile b64_result* r = res;
+  r->first_bad = (int64_t)m;
+  r->outlen = 0;
+  r->status = B64_ERR_TIMEOUT;
+}
+
 struct GeneralArgs {
   const uint8_t* src;
   uint64_t m;
   uint8_t* dst;
   b64_result* res;
   WsHeader* hdr;
-  int64_t* prefix;  // ntiles + 1 entries: tile counts, then their exclusive prefix
+  int64_t* prefix;  // ntiles + 1 entries: warp tile counts, then their exclusive prefix
+  int64_t* blk;     // kMaxWsCtas entries: per-CTA totals of the counts
   uint8_t* packed;  // the kept characters (16-byte aligned)
-  int64_t ntiles;
   uint32_t flags;
   uint64_t wait_ns;
 };
 
-// The general path, one cooperative launch; returns at once unless
-// use_general is set. Phases, between grid barriers: (1) each tile's kept
-// characters counted; (2) CTA 0 turns the counts into their exclusive
-// prefix (prefix[ntiles] = m', the compacted length); (3) each tile packed
-// at its prefix; (4) the packed characters decoded (Algorithm 2: units of 16
-// characters, then whole quads, then the final group), the first bad index
-// reduced in compacted offsets; (5) CTA 0 writes the status with first_bad
-// mapped to an original offset (m on success).
-__global__ void __launch_bounds__(kWsThreads) k_ws_general(GeneralArgs a) {
-  if (!a.hdr->use_general) return;
-  __shared__ __align__(16) uint8_t buf[kWsTile + 32];
-  __shared__ uint16_t sel[16];
-  __shared__ uint8_t D[256];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u;
-  if (tid < 16) {
-    uint32_t v = 0, r = 0;
-    for (uint32_t k = 0; k < 4; ++k)
-      if (tid & (1u << k)) v |= k << (4 * r++);
-    sel[tid] = (uint16_t)v;
-  }
-  init_tables(nullptr, D, a.flags & kFlagUrl);
-  const int64_t m = (int64_t)a.m, ntiles = a.ntiles;
+// The general path, run by every CTA of the (cooperative) launch over warp
+// tiles of 2048 characters, each warp on its own (no block barriers in the
+// passes over the data, which matters with one CTA per SM). Phases, between
+// grid barriers: (1) each warp tile's kept characters counted; (2) their
+// exclusive prefix (prefix[ntiles] = m', the compacted length): each CTA
+// sums a contiguous range of the counts, then scans it from the sum of the
+// ranges before it; (3) each warp tile packed at its prefix; (4) the packed
+// characters decoded (Algorithm 2: units of 16 characters, then whole
+// quads, then the final group), the first bad index reduced in compacted
+// offsets; (5) CTA 0 writes the status with first_bad mapped to an original
+// offset (m on success). smem: NT / 32 warp buffers of kWarpTile + 32
+// bytes; sel and D as for compact_warp_tile and the decode. Out of line, so
+// that the registers of the line-model loop do not depend on it.
+template <int NT>
+__device__ __noinline__ void general_path(const GeneralArgs a, uint8_t* smem, const uint16_t* sel,
+                                          const uint8_t* D) {
+  constexpr uint32_t kWarps = NT / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const int64_t m = (int64_t)a.m;
+  const int64_t ntiles = tmax<int64_t>(1, (m + kWarpTile - 1) / kWarpTile);
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(&a.res->first_bad);
+  uint32_t cur[16], next[16];
   // (1) counts
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int c = count_tile(a.src, m, tile);
-    if (tid == 0) a.prefix[tile] = c;
+  if (gw < ntiles) load_chars(a.src, m, gw * kWarpTile + (int64_t)kWsPerThread * lane, next);
+  for (int64_t t = gw; t < ntiles; t += nw) {
+    step_chars(a.src, m, t, nw, ntiles, cur, next);
+    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popcll(keep_mask(cur)));
+    if (lane == 0) a.prefix[t] = c;
   }
-  if (!grid_sync(a.hdr, a.wait_ns)) return;
-  // (2) exclusive prefix of the counts, by CTA 0
-  if (blockIdx.x == 0) {
-    const int64_t chunk = (ntiles + kWsThreads - 1) / kWsThreads;
-    const int64_t b = tid * chunk, e = tmin<int64_t>(ntiles, b + chunk);
+  if (!grid_sync(a.hdr, a.wait_ns)) return ws_timed_out(a.res, a.m);
+  // (2) exclusive prefix: per-CTA range totals, then each range scanned
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = tmin<int64_t>(ntiles, (int64_t)blockIdx.x * per);
+  const int64_t r1 = tmin<int64_t>(ntiles, r0 + per);
+  {
     int64_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += a.prefix[i];
-    int64_t total;
-    int64_t run = block_excl_scan64(sum, &total);
-    for (int64_t i = b; i < e; ++i) {
-      const int64_t t = a.prefix[i];
-      a.prefix[i] = run;
-      run += t;
-    }
-    if (tid == 0) a.prefix[ntiles] = total;
+    for (int64_t i = r0 + tid; i < r1; i += NT) sum += a.prefix[i];
+    const int64_t total = block_sum64<NT>(sum);
+    if (tid == 0) a.blk[blockIdx.x] = total;
   }
-  if (!grid_sync(a.hdr, a.wait_ns)) return;
-  // (3) compaction
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    compact_tile(a.src, m, tile, a.prefix[tile], a.packed, buf, sel);
-  if (tid == 0) {
+  if (!grid_sync(a.hdr, a.wait_ns)) return ws_timed_out(a.res, a.m);
+  {
+    int64_t before = 0;
+    for (uint32_t b = tid; b < blockIdx.x; b += NT) before += a.blk[b];
+    int64_t run = block_sum64<NT>(before);
+    for (int64_t i0 = r0; i0 < r1; i0 += NT) {
+      const int64_t i = i0 + tid;
+      const int64_t v = i < r1 ? a.prefix[i] : 0;
+      int64_t total;
+      const int64_t ex = block_excl_scan64<NT>(v, &total);
+      if (i < r1) a.prefix[i] = run + ex;
+      run += total;
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) a.prefix[ntiles] = run;
+  }
+  if (!grid_sync(a.hdr, a.wait_ns)) return ws_timed_out(a.res, a.m);
+  // (3) compaction, each warp into its own buffer
+  uint8_t* wbuf = smem + (size_t)warp * (kWarpTile + 32);
+  if (gw < ntiles) load_chars(a.src, m, gw * kWarpTile + (int64_t)kWsPerThread * lane, next);
+  for (int64_t t = gw; t < ntiles; t += nw) {
+    step_chars(a.src, m, t, nw, ntiles, cur, next);
+    compact_warp_tile(cur, a.prefix[t], a.packed, wbuf, sel);
+  }
+  if (lane == 0) {
     bulk_wait_all();
     // the bulk stores (async proxy) come before the generic reads of phase 4
     asm volatile("fence.proxy.async.global;" ::: "memory");
   }
-  if (!grid_sync(a.hdr, a.wait_ns)) return;
+  if (!grid_sync(a.hdr, a.wait_ns)) return ws_timed_out(a.res, a.m);
   // (4) decode of the packed characters
   const uint64_t mc = (uint64_t)a.prefix[ntiles];
   const uint64_t be = decode_body_end(mc);
   const uint64_t nunits = be / 16;
-  const uint64_t stride = (uint64_t)gridDim.x * kWsThreads;
+  // kPer units per thread and step, all loaded before any is decoded (one
+  // CTA per SM: the loads in flight have to cover the memory latency)
+  constexpr uint32_t kPer = 8;
+  const uint64_t stride = (uint64_t)gridDim.x * NT * kPer;
   unsigned long long bad = ~0ull;
-  for (uint64_t base = (uint64_t)blockIdx.x * kWsThreads; base < nunits; base += stride) {
+  for (uint64_t base = (uint64_t)blockIdx.x * NT * kPer; base < nunits; base += stride) {
     // consecutive lanes own consecutive units and store them together
-    const uint64_t u = base + tid;
-    uint3 o = make_uint3(0, 0, 0);
-    if (u < nunits) {
-      const uint4 w = *reinterpret_cast<const uint4*>(a.packed + 16 * u);
-      uint32_t err = 0;
-      o = dec_unit(w, D, err);
-      if ((err & kBadFlag) && bad == ~0ull) bad = 16 * u + dec_unit_first_bad(w, D);
+    uint4 w[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint64_t u = base + k * NT + tid;
+      w[k] = u < nunits ? *reinterpret_cast<const uint4*>(a.packed + 16 * u) : make_uint4(0, 0, 0, 0);
     }
-    const uint64_t u0 = base + (tid & ~31u);
-    if (u0 < nunits)
-      store12_warp(a.dst + 12 * u0, o, lane, (uint32_t)tmin<uint64_t>(32, nunits - u0));
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint64_t u = base + k * NT + tid;
+      uint3 o = make_uint3(0, 0, 0);
+      if (u < nunits) {
+        uint32_t err = 0;
+        o = dec_unit(w[k], D, err);
+        if ((err & kBadFlag) && bad == ~0ull) bad = 16 * u + dec_unit_first_bad(w[k], D);
+      }
+      const uint64_t u0 = base + k * NT + (tid & ~31u);
+      if (u0 < nunits)
+        store12_warp(a.dst + 12 * u0, o, lane, (uint32_t)tmin<uint64_t>(32, nunits - u0));
+    }
   }
   warp_min_to(first_bad, bad);
   if (blockIdx.x == 0) {
@@ -400,10 +437,10 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_general(GeneralArgs a) {
         q[2] = (uint8_t)v;
       }
     }
-    if (tid == kWsThreads - 1 && be < mc)
+    if (tid == NT - 1 && be < mc)
       a.res->outlen = dec_final_group(a.packed, mc, be, a.dst, D, first_bad, a.flags);
   }
-  if (!grid_sync(a.hdr, a.wait_ns)) return;
+  if (!grid_sync(a.hdr, a.wait_ns)) return ws_timed_out(a.res, a.m);
   // (5) the status, first_bad in original offsets
   if (blockIdx.x == 0 && tid < 32) {
     volatile b64_result* r = a.res;
@@ -442,14 +479,18 @@ constexpr uint32_t kLinePathMark = 0x4C494E45u;
 struct LinesArgs {
   const uint8_t* src;
   uint64_t m;
-  uint8_t* dst;  // 16-byte aligned
+  uint8_t* dst;  // 16-byte aligned unless general is set
   b64_result* res;
   WsHeader* hdr;
+  int64_t* prefix;   // scratch of the general path (see GeneralArgs)
+  int64_t* blk;
+  uint8_t* packed;
+  uint32_t general;  // 1: the general path alone (an output the bulk stores cannot take)
   uint32_t upt;      // 16-character units per thread per tile
   uint32_t stages;   // input stages
   uint32_t flags;
   uint32_t stall;    // test: CTA 0 leaves out its first copy
-  uint64_t wait_ns;  // limit of the stage waits
+  uint64_t wait_ns;  // limit of the stage waits and grid barriers
 };
 
 // Bytes of an input stage for a tile of tile_c kept characters: the kept
@@ -578,15 +619,17 @@ __device__ __forceinline__ bool sep_ok(const LineModel& md, const uint8_t* src, 
 // sits at stage position s0; the bulk copy fills stage positions [ia, ib)
 // (the 16-byte aligned part of the tile's original span that lies inside
 // the input); units [u_lo, u_hi) have their whole window of 16 + w bytes
-// there, the few others read theirs from global memory.
+// there, the few others read theirs from global memory. The units end nsep
+// lines that a kept character follows; their separators are checked once
+// per tile (the r-th follows kept character off + (r + 1) L - c0 - 1).
 struct LineTile {
   uint64_t off;
   uint64_t a0;  // original index of kept character off
   uintptr_t G;
   uint32_t len, body, nu, s0, ia, ib;
-  uint32_t c0;     // position of kept character off in its line
-  uint32_t k_lim;  // kept characters from off to the end of the input, at most 2^30
+  uint32_t c0;  // position of kept character off in its line
   uint32_t u_lo, u_hi;
+  uint32_t nsep;
 };
 
 // Window of unit u: p = kept characters from the unit start to its line
@@ -611,7 +654,12 @@ __device__ __forceinline__ void line_tile(const LineModel& md, const LinesArgs& 
   g.nu = g.body / 16u;
   g.a0 = md.orig(g.off);
   g.c0 = md.w ? (uint32_t)(g.off - __umul64hi(g.off, md.inv_L) * md.L) : 0u;
-  g.k_lim = (uint32_t)tmin<uint64_t>(md.mc - g.off, 1u << 30);
+  g.nsep = 0;
+  if (md.w && g.nu) {  // lines j with off <= (j + 1) L - 1 < off + 16 nu and (j + 1) L < mc
+    const uint64_t ja = __umul64hi(g.off, md.inv_L);
+    const uint64_t jb = tmin(__umul64hi(g.off + 16ull * g.nu, md.inv_L), __umul64hi(md.mc - 1, md.inv_L));
+    g.nsep = jb > ja ? (uint32_t)(jb - ja) : 0u;
+  }
   const uintptr_t base = reinterpret_cast<uintptr_t>(a.src);
   const uintptr_t A = base + g.a0;
   g.G = A & ~(uintptr_t)15;
@@ -643,12 +691,10 @@ __device__ __forceinline__ void line_tile(const LineModel& md, const LinesArgs& 
 }
 
 // The unit's 16 kept characters from its window A (bytes [0, 20)): the W
-// separator bytes at window position p are cut out when p < 16. The
-// separator that ends the unit's line (p <= 16) must be whitespace when a
-// kept character follows it (k_rel + p < k_lim); else *bad_sep is set.
+// separator bytes at window position p are cut out when p < 16 (the
+// separators themselves are checked by lines_separators).
 template <uint32_t W, bool WORDCUT>
-__device__ __forceinline__ uint4 cut_unit(const uint32_t (&A)[5], uint32_t p, uint32_t k_rel,
-                                          uint32_t k_lim, const uint8_t* D, bool& bad_sep) {
+__device__ __forceinline__ uint4 cut_unit(const uint32_t (&A)[5], uint32_t p) {
   uint32_t V[4] = {A[0], A[1], A[2], A[3]};
   if (W) {
     const uint32_t pp = min(p, 16u);
@@ -665,18 +711,6 @@ __device__ __forceinline__ uint4 cut_unit(const uint32_t (&A)[5], uint32_t p, ui
         V[i] = (A[i] & keep) | (shifted & ~keep);
       }
     }
-    uint32_t x;
-    if (WORDCUT) {
-      x = p <= 4u ? A[1] : p <= 8u ? A[2] : p <= 12u ? A[3] : A[4];
-    } else {
-      const uint32_t qi = min(p, 16u) >> 2, sh = 8u * (p & 3u);
-      const uint32_t lo = qi == 0 ? A[0] : qi == 1 ? A[1] : qi == 2 ? A[2] : qi == 3 ? A[3] : A[4];
-      const uint32_t hi = qi == 0 ? A[1] : qi == 1 ? A[2] : qi == 2 ? A[3] : A[4];
-      x = __funnelshift_r(lo, hi, sh);
-    }
-    const uint32_t c1 = W > 1 ? (x >> 8) & 0xFFu : x & 0xFFu;
-    const bool ws = (D[x & 0xFFu] & D[c1] & kWsClass) != 0;
-    bad_sep |= p <= 16u && k_rel + p < k_lim && !ws;
   }
   return make_uint4(V[0], V[1], V[2], V[3]);
 }
@@ -696,12 +730,11 @@ __device__ __forceinline__ void stage_window(const uint8_t* st, uint32_t su, uin
 }
 
 // The unit's 16 kept characters, from the stage or (outside [u_lo, u_hi))
-// from global memory; bad_sep as for cut_unit.
+// from global memory.
 template <uint32_t W, bool WORDCUT>
 __device__ __forceinline__ uint4 unit_chars(const LineModel& md, const LineTile& g,
                                             const uint8_t* st, const uint8_t* src, uint64_t m,
-                                            uint32_t u, const uint8_t* D, bool& bad_sep,
-                                            uint32_t& p, uint32_t& su) {
+                                            uint32_t u, uint32_t& p, uint32_t& su) {
   unit_geom(md, g, W, u, p, su);
   uint32_t A[5];
   if (u >= g.u_lo && u < g.u_hi) {
@@ -712,7 +745,7 @@ __device__ __forceinline__ uint4 unit_chars(const LineModel& md, const LineTile&
 #pragma unroll
     for (int i = 0; i < 5; ++i) A[i] = G6[i];
   }
-  return cut_unit<W, WORDCUT>(A, p, 16u * u, g.k_lim, D, bad_sep);
+  return cut_unit<W, WORDCUT>(A, p);
 }
 
 // What a classification found: a byte that breaks the model, and the least
@@ -747,19 +780,17 @@ __device__ __noinline__ Found lines_edge_units(const LineModel md, const LineTil
                                                const uint8_t* src, uint64_t m, uint32_t* ob,
                                                const uint8_t* D) {
   Found f{false, ~0ull};
-  bool bad_sep = false;
   const uint32_t n_lo = g.u_lo, n_hi = g.nu - g.u_hi;
   for (uint32_t i = threadIdx.x; i < n_lo + n_hi; i += NT) {
     const uint32_t u = i < n_lo ? i : g.u_hi + (i - n_lo);
     uint32_t p, su, err = 0;
-    const uint4 v = unit_chars<W, WORDCUT>(md, g, nullptr, src, m, u, D, bad_sep, p, su);
+    const uint4 v = unit_chars<W, WORDCUT>(md, g, nullptr, src, m, u, p, su);
     const uint3 o = dec_unit(v, D, err);
     ob[3 * u] = o.x;
     ob[3 * u + 1] = o.y;
     ob[3 * u + 2] = o.z;
     if (err & kBadFlag) classify_unit<W>(v, g.a0 + (su - g.s0), min(p, 16u), D, f);
   }
-  f.viol |= bad_sep;
   return f;
 }
 
@@ -772,12 +803,39 @@ __device__ __noinline__ Found lines_rescan(const LineModel md, const LineTile g,
                                            const uint8_t* D) {
   Found f{false, ~0ull};
   for (uint32_t u = g.u_lo + threadIdx.x - 32u; threadIdx.x >= 32u && u < g.u_hi; u += NT - 32) {
-    bool bad_sep = false;
     uint32_t p, su;
-    const uint4 v = unit_chars<W, WORDCUT>(md, g, st, src, m, u, D, bad_sep, p, su);
+    const uint4 v = unit_chars<W, WORDCUT>(md, g, st, src, m, u, p, su);
     classify_unit<W>(v, g.a0 + (su - g.s0), min(p, 16u), D, f);
   }
   return f;
+}
+
+// The separators of the lines that the tile's units end (when a kept
+// character follows) are whitespace: nsep of them, one per thread at a time,
+// the r-th at stage position s0 + (r + 1) L - c0 + W r (read from global
+// memory when it lies outside the staged bytes). One pass per tile costs
+// far less than a check in every unit, since a line holds several units.
+template <int NT, uint32_t W>
+__device__ __forceinline__ bool lines_separators(const LineModel& md, const LineTile& g,
+                                                 const uint8_t* st, const uint8_t* src,
+                                                 const uint8_t* D) {
+  if (W == 0) return false;
+  bool bad = false;
+  const uint32_t step = md.L + W;
+  for (uint32_t r = threadIdx.x; r < g.nsep; r += NT) {
+    const uint32_t sp = g.s0 + md.L - g.c0 + r * step;
+    uint32_t c0, c1;
+    if (sp >= g.ia && sp + W <= g.ib) {
+      c0 = st[sp];
+      c1 = st[sp + W - 1];
+    } else {
+      const uint8_t* q = src + (g.a0 + (sp - g.s0));
+      c0 = q[0];
+      c1 = q[W - 1];
+    }
+    bad |= (D[c0] & D[c1] & kWsClass) == 0;
+  }
+  return bad;
 }
 
 // Decodes the whole units [0, nu) of a staged tile into ob (12 bytes per
@@ -786,9 +844,9 @@ __device__ __noinline__ Found lines_rescan(const LineModel md, const LineTile g,
 // at the tile's barrier): its window of 16 + W
 // bytes from the stage (a 16-byte load with no line breaks and an aligned
 // input, else aligned words and funnel shifts), the separator that ends a
-// line inside it cut out and checked to be whitespace. W: separator bytes
-// (0: no line breaks); WORDCUT: L is a multiple of 4, so a line ends on a
-// word of the window (whole-word selects), else the cut takes byte masks.
+// line inside it cut out (and checked in a pass of its own). W: separator
+// bytes (0: no line breaks); WORDCUT: L is a multiple of 4, so a line ends on
+// a word of the window (whole-word selects), else the cut takes byte masks.
 template <int NT, uint32_t W, bool WORDCUT>
 __device__ __forceinline__ void lines_tile_units(const LineModel& md, const LineTile& g,
                                                  const uint8_t* st, const uint8_t* src,
@@ -805,20 +863,19 @@ __device__ __forceinline__ void lines_tile_units(const LineModel& md, const Line
       ob[3 * u + 2] = o.z;
     }
   } else {
-    bool bad_sep = false;
 #pragma unroll 2
     for (uint32_t u = g.u_lo + threadIdx.x - 32u; threadIdx.x >= 32u && u < g.u_hi; u += NT - 32) {
       uint32_t p, su;
       unit_geom(md, g, W, u, p, su);
       uint32_t A[5];
       stage_window<W>(st, su, A);
-      const uint4 v = cut_unit<W, WORDCUT>(A, p, 16u * u, g.k_lim, D, bad_sep);
+      const uint4 v = cut_unit<W, WORDCUT>(A, p);
       const uint3 o = dec_unit(v, D, err);
       ob[3 * u] = o.x;
       ob[3 * u + 1] = o.y;
       ob[3 * u + 2] = o.z;
     }
-    if (bad_sep) viol = true;
+    if (lines_separators<NT, W>(md, g, st, src, D)) viol = true;
   }
   if (err & kBadFlag) {
     const Found f = lines_rescan<NT, W, WORDCUT>(md, g, st, src, m, D);
@@ -833,31 +890,30 @@ __device__ __forceinline__ void lines_tile_units(const LineModel& md, const Line
 }
 
 // Runs in every CTA after its tiles: a CTA that saw a byte break the model
-// raises the violation flag; the last CTA to arrive then either hands the
-// call to the general path (the result back to its cleared state) or
-// writes the status, first_bad mapped to original offsets.
-__device__ void lines_finish(const LinesArgs& a, const LineModel& md, bool timed_out, bool viol) {
+// raises the violation flag (one whose wait ran out, the fault word), then
+// all CTAs meet at a grid barrier. True if some CTA raised the flag: the
+// result is back to its cleared state and the general path decodes the
+// input instead. Else CTA 0 has written the status, first_bad mapped to
+// original offsets.
+__device__ bool lines_finish(const LinesArgs& a, const LineModel& md, bool timed_out, bool viol) {
   if (__syncthreads_or(viol) && threadIdx.x == 0) atomicOr(&a.hdr->violation, 1u);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  if (timed_out) atomicOr(&g_ws_fault, 1u);
-  const unsigned prev = atomicAdd(&a.res->internal, 1u);
-  if (prev != gridDim.x - 2u) return;  // counter starts at 0xFFFFFFFF
-  __threadfence();
+  if (timed_out && threadIdx.x == 0) atomicOr(&g_ws_fault, 1u);
+  if (!grid_sync(a.hdr, a.wait_ns)) {
+    ws_timed_out(a.res, a.m);
+    return false;
+  }
+  const bool broke = *reinterpret_cast<volatile uint32_t*>(&a.hdr->violation) != 0;
+  if (blockIdx.x != 0 || threadIdx.x != 0) return broke;
   volatile b64_result* r = a.res;
   const bool fault = atomicAdd(&g_ws_fault, 0u) != 0;
-  const bool broke = atomicAdd(&a.hdr->violation, 0u) != 0;
-  if (fault) {
-    r->first_bad = (int64_t)a.m;
-    r->outlen = 0;
-    r->status = B64_ERR_TIMEOUT;
-  } else if (broke) {
+  if (broke) {
     r->first_bad = -1;
     r->outlen = -1;
     r->status = -1;
-    r->internal = 0xFFFFFFFFu;
-    a.hdr->use_general = 1;
+  } else if (fault) {
+    r->first_bad = (int64_t)a.m;
+    r->outlen = 0;
+    r->status = B64_ERR_TIMEOUT;
   } else {
     const uint64_t be = decode_body_end(md.mc);
     const unsigned long long fb =
@@ -872,41 +928,20 @@ __device__ void lines_finish(const LinesArgs& a, const LineModel& md, bool timed
     r->internal = kLinePathMark;
   }
   __threadfence();
+  return broke;
 }
 
-// The one-pass decode under the line model (see the top of this file).
+// The one-pass decode under the line model md (see the top of this file),
+// by every CTA; true if a byte broke the model in some CTA (lines_finish).
 template <int NT>
-__global__ void __launch_bounds__(NT, 1) k_ws_lines(LinesArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint8_t D[256];
-  __shared__ __align__(8) uint64_t full[kMaxLineStages];
-  __shared__ LineTile tiles[kMaxLineStages];
-  __shared__ LineModel md_s;
-  __shared__ uint32_t s_first, s_trail;
-
+__device__ __forceinline__ bool lines_decode(const LinesArgs& a, const LineModel md,
+                                             const uint8_t* D, uint64_t* full, LineTile* tiles,
+                                             uint8_t* smem) {
   const uint32_t tid = threadIdx.x;
   const uint32_t S = a.stages;
   const uint32_t tile_c = NT * a.upt * 16u;
   const uint32_t tile_o = NT * a.upt * 12u;
   const uint32_t stage_b = line_stage_bytes(tile_c);
-  if (tid == 0) {
-    for (uint32_t s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    fence_mbar_init();
-    s_first = ~0u;
-  }
-  init_tables(nullptr, D, a.flags & kFlagUrl);
-  if (tid == 0) {  // whitespace keeps the invalid flag and gets its class bit
-    D[0x20] |= kWsClass;
-    D[0x0A] |= kWsClass;
-    D[0x0D] |= kWsClass;
-  }
-  __syncthreads();
-  find_line_model<NT>(a.src, a.m, D, md_s, &s_first, &s_trail);
-  const LineModel md = md_s;
-  if (!md.ok) {
-    if (blockIdx.x == 0 && tid == 0) a.hdr->use_general = 1;
-    return;
-  }
   const uint64_t mc = md.mc;
   const uint64_t body_end = decode_body_end(mc);
   const uint64_t ntiles = (mc + tile_c - 1) / tile_c;
@@ -1049,13 +1084,62 @@ __global__ void __launch_bounds__(NT, 1) k_ws_lines(LinesArgs a) {
   }
   if (tid == 0) bulk_wait_all();
   warp_min_to(reinterpret_cast<unsigned long long*>(&a.res->first_bad), bad);
-  lines_finish(a, md, timed_out, viol);
+  return lines_finish(a, md, timed_out, viol);
+}
+
+// The whitespace-removing decode, one cooperative launch: the line-model
+// decode, unless the host asked for the general path (an output the bulk
+// stores cannot take) or the input has no line model the kernel can use;
+// the general path when either holds or a byte broke the model.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_ws_lines(LinesArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint8_t D[256];
+  __shared__ uint16_t sel[16];
+  __shared__ __align__(8) uint64_t full[kMaxLineStages];
+  __shared__ LineTile tiles[kMaxLineStages];
+  __shared__ LineModel md_s;
+  __shared__ uint32_t s_first, s_trail;
+
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) {
+    for (uint32_t s = 0; s < a.stages; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+    s_first = ~0u;
+  }
+  if (tid < 16) {  // byte_perm selectors of the general path's compaction
+    uint32_t v = 0, r = 0;
+    for (uint32_t k = 0; k < 4; ++k)
+      if (tid & (1u << k)) v |= k << (4 * r++);
+    sel[tid] = (uint16_t)v;
+  }
+  init_tables(nullptr, D, a.flags & kFlagUrl);
+  if (tid == 0) {  // whitespace keeps the invalid flag and gets its class bit
+    D[0x20] |= kWsClass;
+    D[0x0A] |= kWsClass;
+    D[0x0D] |= kWsClass;
+  }
+  __syncthreads();
+  // the same decisions in every CTA
+  bool general = a.general != 0;
+  if (!general) {
+    find_line_model<NT>(a.src, a.m, D, md_s, &s_first, &s_trail);
+    general = !md_s.ok;
+  }
+  if (!general) general = lines_decode<NT>(a, md_s, D, full, tiles, smem);
+  if (general) {
+    const GeneralArgs ga{a.src, a.m, a.dst,   a.res,   a.hdr,
+                         a.prefix, a.blk, a.packed, a.flags, a.wait_ns};
+    general_path<NT>(ga, smem, sel, D);
+  }
 }
 
 }  // namespace
 
 namespace {
 
+// One cooperative launch (the CTAs meet at grid barriers), one CTA per SM at
+// most and at most one per tile of kept characters.
 template <int NT>
 cudaError_t launch_lines_nt(const LinesArgs& a0, const TileConfig& c, cudaStream_t stream) {
   cudaError_t e;
@@ -1071,9 +1155,11 @@ cudaError_t launch_lines_nt(const LinesArgs& a0, const TileConfig& c, cudaStream
   if (e != cudaSuccess) return e;
   if (bps < 1) return cudaErrorInvalidConfiguration;
   const uint64_t ntiles = std::max<uint64_t>(1, (a.m + tile_c - 1) / tile_c);
-  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)di->sm_count * bps);
-  k_ws_lines<NT><<<grid, NT, smem, stream>>>(a);
-  return cudaGetLastError();
+  const int grid = (int)std::min<uint64_t>(
+      {ntiles, (uint64_t)di->sm_count * bps, (uint64_t)kMaxWsCtas});
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_ws_lines<NT>), grid, NT, args,
+                                     smem, stream);
 }
 
 cudaError_t launch_lines(const LinesArgs& a, const TileConfig& c, cudaStream_t stream) {
@@ -1081,22 +1167,19 @@ cudaError_t launch_lines(const LinesArgs& a, const TileConfig& c, cudaStream_t s
   return c.threads == 256 ? launch_lines_nt<256>(a, c, stream) : launch_lines_nt<512>(a, c, stream);
 }
 
-// The general path: one cooperative launch (its CTAs wait on one another at
-// grid barriers), at most as many CTAs as fit the GPU at once and at most one
-// per tile.
-cudaError_t launch_general(GeneralArgs& ga, cudaStream_t stream) {
-  cudaError_t e;
-  const DeviceInfo* di = device_info(&e);
-  if (!di) return e;
-  int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_ws_general, kWsThreads, 0);
-  if (e != cudaSuccess) return e;
-  if (bps < 1) return cudaErrorInvalidConfiguration;
-  const int grid = (int)std::min<int64_t>((int64_t)di->sm_count * bps, ga.ntiles);
-  void* args[] = {&ga};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_ws_general), grid, kWsThreads,
-                                     args, 0, stream);
-}
+// Scratch of the whitespace decode, kept per device between calls (a
+// stream-ordered allocation of about m bytes in every call cost about 20 us
+// of host and device time on a 367 MB input). A call on another stream is
+// ordered after the last user by an event; while the stream captures a
+// graph, the call allocates from the stream-ordered allocator instead.
+struct WsScratch {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+constexpr int kMaxDevices = 128;
+std::mutex g_ws_mu;
+WsScratch g_ws_scratch[kMaxDevices];
 
 }  // namespace
 
@@ -1116,39 +1199,107 @@ bool ws_lines_config_valid(const TileConfig& c) {
          c.stages <= (int)kMaxLineStages;
 }
 
+// The input stages and two output buffers of the line-model decode, and at
+// least the general path's packing buffer (which reuses them).
 size_t ws_lines_smem_bytes(const TileConfig& c) {
   const uint32_t tile_c = (uint32_t)c.threads * c.upt * 16u;
-  return (size_t)c.stages * line_stage_bytes(tile_c) + 2 * (size_t)c.threads * c.upt * 12u;
+  const size_t lines =
+      (size_t)c.stages * line_stage_bytes(tile_c) + 2 * (size_t)c.threads * c.upt * 12u;
+  return std::max(lines, (size_t)c.threads / 32 * (kWarpTile + 32));
 }
 
+// Header, packed characters, warp tile prefix and per-CTA totals.
 size_t ws_scratch_bytes(uint64_t m) {
-  const int64_t ntiles = std::max<int64_t>(1, ((int64_t)m + kWsTile - 1) / kWsTile);
-  return kWsHeaderBytes + ((m + 255) & ~255ull) + (size_t)(ntiles + 1) * 8;
+  const int64_t ntiles = std::max<int64_t>(1, ((int64_t)m + kWarpTile - 1) / kWarpTile);
+  return kWsHeaderBytes + ((m + 255) & ~255ull) + (size_t)(ntiles + 1 + kMaxWsCtas) * 8;
 }
 
-// Enqueues the whitespace-removing decode; *d_result has been cleared. The
-// line-model kernel runs first when dst is 16-byte aligned; the general
-// path's kernels follow on the stream and return at once unless the line
-// model failed (or was not tried).
+// Enqueues the whitespace-removing decode into the given scratch;
+// *d_result has been cleared. One launch: the line-model decode when dst is
+// 16-byte aligned, with the general path in the same kernel when the model
+// does not hold; the general path alone otherwise.
 cudaError_t decode_ws_launch(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
                              void* scratch, uint32_t flags, cudaStream_t stream) {
-  const int64_t ntiles = std::max<int64_t>(1, ((int64_t)m + kWsTile - 1) / kWsTile);
   WsHeader* hdr = static_cast<WsHeader*>(scratch);
   uint8_t* packed = static_cast<uint8_t*>(scratch) + kWsHeaderBytes;
   int64_t* prefix = reinterpret_cast<int64_t*>(packed + ((m + 255) & ~255ull));
+  const int64_t ntiles = std::max<int64_t>(1, ((int64_t)m + kWarpTile - 1) / kWarpTile);
+  int64_t* blk = prefix + ntiles + 1;
   const uint32_t dflags = flags & ~(uint32_t)B64_FLAG_SKIP_WS;
-  const bool lines = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
-  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
-  if (e == cudaSuccess && !lines) e = cudaMemsetAsync(&hdr->use_general, 1, 1, stream);
+  const uint32_t general = (reinterpret_cast<uintptr_t>(dst) & 15u) != 0;
+  const cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
   if (e != cudaSuccess) return e;
-  if (lines) {
-    const WaitTest wt = wait_test();
-    LinesArgs a{src, m, dst, d_result, hdr, 0, 0, dflags, wt.stall, wt.limit_ns};
-    e = launch_lines(a, ws_lines_config(m), stream);
+  const WaitTest wt = wait_test();
+  const LinesArgs a{src, m, dst, d_result, hdr, prefix, blk, packed, general,
+                    0, 0, dflags, wt.stall, wt.limit_ns};
+  return launch_lines(a, ws_lines_config(m), stream);
+}
+
+// Enqueues the whitespace-removing decode with the device's kept scratch
+// (or, under graph capture, a stream-ordered allocation).
+cudaError_t decode_ws_enqueue(const uint8_t* src, uint64_t m, uint8_t* dst, b64_result* d_result,
+                              uint32_t flags, cudaStream_t stream) {
+  const size_t need = ws_scratch_bytes(m);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) {
+    void* scratch = nullptr;
+    e = cudaMallocAsync(&scratch, need, stream);
     if (e != cudaSuccess) return e;
+    e = decode_ws_launch(src, m, dst, d_result, scratch, flags, stream);
+    const cudaError_t ef = cudaFreeAsync(scratch, stream);
+    return e != cudaSuccess ? e : ef;
   }
-  GeneralArgs ga{src, m, dst, d_result, hdr, prefix, packed, ntiles, dflags, wait_test().limit_ns};
-  return launch_general(ga, stream);
+  const DeviceInfo* di = device_info(&e);
+  if (!di) return e;
+  if (di->device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  WsScratch& w = g_ws_scratch[di->device];
+  if (!w.done) {
+    e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      w.done = nullptr;
+      return e;
+    }
+  }
+  if (w.cap < need) {
+    if (w.p) {
+      e = cudaEventSynchronize(w.done);
+      if (e == cudaSuccess) e = cudaFree(w.p);
+      if (e != cudaSuccess) return e;
+      w.p = nullptr;
+      w.cap = 0;
+    }
+    const size_t cap = (need + (16u << 20) - 1) & ~(size_t)((16u << 20) - 1);
+    e = cudaMalloc(&w.p, cap);
+    if (e != cudaSuccess) {
+      w.p = nullptr;
+      return e;
+    }
+    w.cap = cap;
+  }
+  e = cudaStreamWaitEvent(stream, w.done, 0);
+  if (e == cudaSuccess) e = decode_ws_launch(src, m, dst, d_result, w.p, flags, stream);
+  const cudaError_t er = cudaEventRecord(w.done, stream);
+  return e != cudaSuccess ? e : er;
+}
+
+// Frees the current device's kept scratch once its last user is done.
+cudaError_t ws_release_scratch() {
+  cudaError_t e;
+  const DeviceInfo* di = device_info(&e);
+  if (!di) return e;
+  if (di->device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  WsScratch& w = g_ws_scratch[di->device];
+  if (!w.p) return cudaSuccess;
+  e = cudaEventSynchronize(w.done);
+  if (e == cudaSuccess) e = cudaFree(w.p);
+  if (e != cudaSuccess) return e;
+  w.p = nullptr;
+  w.cap = 0;
+  return cudaSuccess;
 }
 
 int ws_read_and_clear_fault(unsigned int* out) {

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
         "b64_status_str": (ctypes.c_char_p, [i32]),
         "b64_last_error": (ctypes.c_char_p, []),
         "b64_device_fault": (i32, []),
+        "b64_release_scratch": (i32, []),
         "b64_test_stall_copies": (i32, [i32, ctypes.c_uint64]),
         "b64_shape_get": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
         "b64_shape_set": (i32, [i32, i64, i64, ctypes.POINTER(b64_shape)]),
@@ -167,6 +168,14 @@ def b64_decoded_cap(m: int) -> int:
 
 def b64_device_fault() -> int:
     return int(lib().b64_device_fault())
+
+
+def b64_release_scratch() -> None:
+    """Frees the scratch that the whitespace decode keeps on the current
+    device (after its last user)."""
+    st = int(lib().b64_release_scratch())
+    if st != B64_OK:
+        raise Gb64Error(st, b64_last_error())
 
 
 def b64_test_stall_copies(stall: bool, wait_limit_ns: int = 0) -> None:

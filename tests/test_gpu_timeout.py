@@ -107,3 +107,34 @@ def test_staged_batch_times_out_then_recovers(gb64, oracle):
                                                                  "stages", "blocks_per_sm",
                                                                  "tile")})
     assert gb64.b64_device_fault() == 0
+
+
+def test_whitespace_decode_times_out_then_recovers(gb64, oracle):
+    """The line-model kernel of the whitespace decode: CTA 0's first stage
+    wait runs out, the CTAs still meet at the grid barrier, and the call
+    reports B64_ERR_TIMEOUT with first_bad = m; then the same input decodes
+    exactly through the line path."""
+    import base64
+
+    import torch
+
+    raw = W.uniform_bytes(3 << 20, 44)
+    e = base64.b64encode(raw.tobytes())
+    s = b"\r\n".join(e[i:i + 76] for i in range(0, len(e), 76)) + b"\r\n"
+    src = torch.from_numpy(np.frombuffer(s, dtype=np.uint8).copy()).cuda()
+    dst = torch.zeros(raw.size + 16, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    with stalled(gb64):
+        gb64.b64_decode_async_ex(src, dst, res, 8)
+        torch.cuda.synchronize()
+        st, outlen, fb = gb64.parse_result(res)
+        assert (st, outlen, fb) == (gb64.B64_ERR_TIMEOUT, 0, len(s))
+        assert gb64.b64_device_fault() == gb64.B64_ERR_TIMEOUT
+    assert gb64.b64_device_fault() == 0
+    gb64.b64_decode_async_ex(src, dst, res, 8)
+    torch.cuda.synchronize()
+    assert gb64.parse_result(res) == (0, raw.size, len(s))
+    assert int(res.view(torch.int32)[5].item()) & 0xFFFFFFFF == 0x4C494E45
+    assert np.array_equal(dst[:raw.size].cpu().numpy(), raw)
+    ost, oout, ofb = oracle.decode_ex(s, 8)
+    assert (ost, ofb) == (0, len(s)) and np.array_equal(oout, raw)

@@ -201,3 +201,74 @@ def test_large_mime(gb64, oracle):
     st, outlen, fb, d, took = run(gb64, t)
     assert (st, outlen, took) == (0, raw.size, False)
     assert torch.equal(torch.from_numpy(d), torch.from_numpy(raw))
+
+
+@pytest.mark.parametrize("shape", [(256, 4, 3), (256, 1, 6), (512, 1, 4), (512, 2, 4),
+                                   (512, 4, 3), (512, 7, 2)])
+def test_line_kernel_shapes(gb64, oracle, shape):
+    """Every tile shape the shape table accepts for the line-model kernel
+    (threads, 16-character units per thread, stages) decodes exactly: MIME
+    and PEM lines, unaligned input, errors."""
+    from paper_1704_00605_gb300.workloads import NON_ALPHABET_NON_PAD
+
+    threads, upt, stages = shape
+    kind = gb64.B64_KIND_DECODE_WS
+    rng = np.random.default_rng(sum(shape))
+    cases = []
+    for n, L, sep in ((300_001, 76, b"\r\n"), (200_000, 64, b"\n"), (150_000, 57, b"\n")):
+        e = base64.b64encode(rng.integers(0, 256, n, dtype=np.uint8).tobytes())
+        cases.append(wrap(e, L, sep, sep))
+    t = bytearray(cases[0])
+    for q in rng.integers(0, len(t), 3):
+        if t[q] not in b"\r\n":
+            t[q] = int(NON_ALPHABET_NON_PAD[int(rng.integers(0, 191))])
+    cases.append(bytes(t))
+    saved = [gb64.b64_shape_get(kind, len(c), 1) for c in cases]
+    try:
+        for k, c in enumerate(cases):
+            gb64.b64_shape_set(kind, len(c), 1, threads=threads, units_per_thread=upt,
+                               stages=stages, blocks_per_sm=0, tile=threads * upt * 16)
+            check(gb64, oracle, c, off=k * 5 % 16, line=True)
+    finally:
+        for c, sh in zip(cases, saved):
+            gb64.b64_shape_set(kind, len(c), 1, **{f: sh[f] for f in (
+                "threads", "units_per_thread", "stages", "blocks_per_sm", "tile")})
+
+
+def test_line_kernel_shape_validation(gb64):
+    kind = gb64.B64_KIND_DECODE_WS
+    for bad in ((128, 4, 3), (1024, 2, 3), (512, 9, 2), (512, 4, 1), (512, 4, 7),
+                (512, 8, 2)):  # the last needs more shared memory than a CTA has
+        with pytest.raises(gb64.Gb64Error):
+            gb64.b64_shape_set(kind, 1 << 20, 1, threads=bad[0], units_per_thread=bad[1],
+                               stages=bad[2], blocks_per_sm=0, tile=bad[0] * bad[1] * 16)
+
+
+@pytest.mark.parametrize("threads", [256, 512])
+def test_general_path_in_each_block_size(gb64, oracle, threads):
+    """The general path runs in the line kernel's own launch, so with its
+    block size: sprinkled whitespace (no line model), a model broken late in
+    a long input, and an output the bulk stores cannot take (general path
+    alone) decode exactly with both block sizes."""
+    kind = gb64.B64_KIND_DECODE_WS
+    rng = np.random.default_rng(threads)
+    e = base64.b64encode(rng.integers(0, 256, 400_000, dtype=np.uint8).tobytes())
+    sprinkled = bytearray()
+    for i in range(0, len(e), 40):
+        sprinkled += e[i:i + 40] + b" \r\n"[int(rng.integers(0, 3)):][:int(rng.integers(0, 3))]
+    mime = wrap(e, 76, b"\r\n", b"\r\n")
+    late = mime[:len(mime) - 777] + b" " + mime[len(mime) - 777:]
+    cases = [bytes(sprinkled), late, mime]
+    saved = [gb64.b64_shape_get(kind, len(c), 1) for c in cases]
+    try:
+        for c in cases:
+            gb64.b64_shape_set(kind, len(c), 1, threads=threads, units_per_thread=2, stages=3,
+                               blocks_per_sm=0, tile=threads * 2 * 16)
+        check(gb64, oracle, cases[0], line=False)
+        check(gb64, oracle, cases[1], off=3, line=False)
+        check(gb64, oracle, cases[2], dst_off=5, line=False)
+        check(gb64, oracle, cases[2], line=True)
+    finally:
+        for c, sh in zip(cases, saved):
+            gb64.b64_shape_set(kind, len(c), 1, **{f: sh[f] for f in (
+                "threads", "units_per_thread", "stages", "blocks_per_sm", "tile")})
