@@ -936,7 +936,8 @@ def run_whitespace(args, d: Dist, src=None, plain_us=None):
     the encoding of 256 MiB of uniform random bytes (76 characters and CR LF
     per line: 367,332,732 characters): CUDA-event time per call, the
     algorithmic bytes (characters read + bytes written) against the HBM
-    peak, and an exact round trip."""
+    peak, and an exact round trip; then the same input with one space
+    inside a line, which breaks the line model and takes the general path."""
     import torch
 
     import paper_1704_00605_gb300 as pkg
@@ -970,6 +971,16 @@ def run_whitespace(args, d: Dist, src=None, plain_us=None):
     line_path = (int(res.view(torch.int32)[5].item()) & 0xFFFFFFFF) == 0x4C494E45
     assert (st, outlen, fb) == (0, n, wrapped.numel()), (st, outlen, fb)
     assert torch.equal(dec[:n], src)
+    # the same lines with one space inside the second line: the model breaks
+    # in the first tile, so the call decodes the input by the general path
+    broken = torch.cat([wrapped[:100], wrapped.new_tensor([32]), wrapped[100:]])
+    dec.zero_()
+    g_us = timed(lambda: g.b64_decode_async_ex(broken, dec, res, 8), 10)
+    st, outlen, fb = g.parse_result(res)
+    g_line = (int(res.view(torch.int32)[5].item()) & 0xFFFFFFFF) == 0x4C494E45
+    assert (st, outlen, fb, g_line) == (0, n, broken.numel(), False), (st, outlen, fb, g_line)
+    assert torch.equal(dec[:n], src)
+    del broken
     if plain_us is None:
         plain_us = timed(lambda: g.b64_decode_async(enc, dec, res), 20)
     peak, peak_kind = measured_peaks()
@@ -979,7 +990,10 @@ def run_whitespace(args, d: Dist, src=None, plain_us=None):
             "alg_bytes": int(alg), "hbm_gbs": round(alg / w_us / 1e3, 1),
             "frac": round(alg / w_us / 1e3 / peak, 4), "peak": peak,
             "peak_kind": f"{peak_kind} hbm_gbs", "line_model_path": line_path,
-            "plain_decode_us": round(plain_us, 2), "gpu_launches_per_call": 2}
+            "general_path_us": round(g_us, 2),
+            "general_path_frac": round((alg + 1) / g_us / 1e3 / peak, 4),
+            "plain_decode_us": round(plain_us, 2),
+            "gpu_launches_per_call": 1, "memsets_per_call": 2}
 
 
 def sweep_line(args, d: Dist):

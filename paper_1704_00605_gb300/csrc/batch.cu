@@ -243,6 +243,22 @@ struct DescMsgs {
   __device__ __forceinline__ void prepare(int64_t) {}
 };
 
+// Whether a packed decode batch takes the flat decode (k_batch_flat: every
+// length a multiple of 4 and a mean length of at least kFlatMinMean
+// characters); the flat kernel, the tile walk and the finish kernel decide
+// alike.
+constexpr int64_t kFlatMinMean = 1024;
+template <class Msgs>
+__device__ __forceinline__ bool flat_batch(const Msgs&, int64_t) {
+  return false;
+}
+template <>
+__device__ __forceinline__ bool flat_batch<PackedMsgs>(const PackedMsgs& ms, int64_t nmsg) {
+  if (nmsg <= 0) return false;
+  const int64_t M = __ldg(ms.in_off + nmsg), Mo = __ldg(ms.out_off + nmsg);
+  return 4 * Mo == 3 * M && M >= kFlatMinMean * nmsg;
+}
+
 // ------------------------------------------------------ warp pipeline
 // Every warp walks its own share of the tiles (see WalkState below). Tile k
 // of message j holds input bytes [t0, t0 + len) of j, t0 = k * tile,
@@ -1020,13 +1036,16 @@ __global__ void __launch_bounds__(NT)
 // (one warp-instruction each, as on one lane), and the tiles' units move
 // straight between global memory and registers, so a warp needs no shared
 // memory, barrier or copy engine, and a tile may be longer than a stage
-// could hold.
+// could hold. after_flat: k_batch_flat ran before; a batch it decoded is
+// left alone.
 template <int NT, int DECODE, class Msgs>
 __global__ void __launch_bounds__(NT)
     k_batch_direct(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ weight_off, TileShape ts,
-                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags) {
+                   int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
+                   uint32_t after_flat) {
   __shared__ uint8_t table[DECODE ? 256 : 64];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (DECODE && after_flat && flat_batch(msgs, nmsg)) return;
   if (DECODE) {
     init_tables(nullptr, table, flags & kFlagUrl);
   } else {
@@ -1057,15 +1076,280 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// ------------------------------------------------------------ flat decode
+// A packed decode batch whose lengths are all multiples of 4 (every padded
+// encoding) has message j's output at exactly 3/4 of its input offset (the
+// capacities 3 floor(m / 4) sum to 3/4 of the characters then, and only
+// then), so the whole batch decodes as one buffer: Algorithm 2 on every
+// quad, by the single-buffer pipeline (one CTA of 512 threads per SM, each
+// CTA a contiguous run of 60 Ki-character tiles staged by TMA two ahead,
+// decoded units staged and stored by TMA). Only the last quad of a message,
+// its final group (where '=' may stand), depends on the message: the finish
+// kernel writes its bytes and checks its rules. Warp 0 issues the copies
+// and marks, in a bitmask beside each stage, the final quads of the
+// messages that end in that tile; a unit that flags a character in a
+// marked quad is no error, any other flagged character is reported at its
+// offset in its message. Batches of shorter messages (mean below
+// kFlatMinMean characters: many ends per tile) and all others are left to
+// the tile walk (k_batch_direct), which checks the same condition.
+constexpr int kFlatThreads = 512;
+constexpr uint32_t kFlatUnits = 8;  // 16-character units per decoding thread per tile
+// warps 1.. decode (warp 0 issues), each of their threads kFlatUnits units
+constexpr uint32_t kFlatTile = (uint32_t)(kFlatThreads - 32) * kFlatUnits * 16u;  // 61,440
+constexpr uint32_t kFlatOut = kFlatTile / 4u * 3u;
+constexpr uint32_t kFlatStages = 2;
+constexpr uint32_t kFlatMaskWords = kFlatTile / 4u / 32u;  // one bit per quad
+
+__host__ __device__ constexpr size_t flat_smem_bytes() {
+  return (size_t)kFlatStages * kFlatTile + 2 * (size_t)kFlatOut;
+}
+
+// The first message j whose end in_off[j + 1] exceeds x (x < in_off[nmsg]),
+// by the whole warp: each round probes 32 evenly spaced ends of the span
+// left and keeps the part between the last one at most x and the first one
+// above it (about five rounds for a million messages).
+__device__ __forceinline__ int64_t first_end_after(const int64_t* in_off, int64_t nmsg, int64_t x,
+                                                   uint32_t lane) {
+  int64_t lo = 0, hi = nmsg - 1;
+  while (hi > lo) {
+    const int64_t span = hi - lo;
+    const bool above = __ldg(in_off + lo + span * lane / 32 + 1) > x;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, above);
+    if (b == 0) {
+      lo = lo + span * 31 / 32 + 1;
+    } else {
+      const int64_t f = __ffs(b) - 1;
+      const int64_t nlo = f ? lo + span * (f - 1) / 32 + 1 : lo;
+      hi = lo + span * f / 32;
+      lo = nlo;
+    }
+  }
+  return lo;
+}
+
+// A unit of a flat tile that flagged a character (quads q0 .. q0 + 3 of the
+// tile): each flagged quad that is not a marked final quad holds an invalid
+// character; its first one goes to its message's first_bad.
+__device__ __noinline__ void flat_flagged(uint4 v, uint32_t q0, const uint32_t* mask, int64_t T0,
+                                          int64_t j_lo, const int64_t* in_off, int64_t nmsg,
+                                          int64_t* first_bad, const uint8_t* D) {
+  for (uint32_t q = 0; q < 4; ++q) {
+    const uint32_t qi = q0 + q;
+    if ((mask[qi >> 5] >> (qi & 31u)) & 1u) continue;
+    const uint32_t x = word_of(v, q);
+    for (uint32_t i = 0; i < 4; ++i) {
+      if (D[(x >> (8u * i)) & 0xFFu] & kBadFlag) {
+        const int64_t p = T0 + 4 * (int64_t)qi + i;
+        int64_t lo = j_lo, hi = nmsg - 1;  // the first message ending after p
+        while (lo < hi) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          if (__ldg(in_off + mid + 1) > p) hi = mid; else lo = mid + 1;
+        }
+        atomicMin(reinterpret_cast<unsigned long long*>(first_bad + lo),
+                  (unsigned long long)(p - __ldg(in_off + lo)));
+        break;
+      }
+    }
+  }
+}
+
+// One tile's place beside its stage (written by warp 0 before the arrive
+// that publishes it).
+struct FlatTile {
+  int64_t T0;    // first character
+  int64_t j_lo;  // first message ending after T0
+  uint32_t len;  // characters
+};
+
+__global__ void __launch_bounds__(kFlatThreads, 1)
+    k_batch_flat(PackedMsgs ms, int64_t nmsg, int64_t* __restrict__ first_bad, uint32_t flags,
+                 WaitTest wt) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint8_t D[256];
+  __shared__ __align__(8) uint64_t full[kFlatStages];
+  __shared__ FlatTile meta[kFlatStages];
+  __shared__ uint32_t fmask[kFlatStages][kFlatMaskWords];
+  constexpr int NT = kFlatThreads;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  if (!flat_batch(ms, nmsg)) return;  // the tile walk decodes the batch
+  if (tid == 0) {  // two arrivals per phase: the copy's (with its bytes), then the mask's
+    for (uint32_t s = 0; s < kFlatStages; ++s) mbar_init(&full[s], 2);
+    fence_mbar_init();
+  }
+  init_tables(nullptr, D, flags & kFlagUrl);
+  __syncthreads();
+  const int64_t M = __ldg(ms.in_off + nmsg);
+  const int64_t ntiles = (M + kFlatTile - 1) / kFlatTile;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t tb = tmin<int64_t>(ntiles, (int64_t)blockIdx.x * per);
+  const int64_t te = tmin<int64_t>(ntiles, tb + per);
+  if (tb >= te) return;
+  uint8_t* outbuf0 = smem + (size_t)kFlatStages * kFlatTile;
+
+  // warp 0: the first message ending after the next tile to issue, and the
+  // lane's two offsets pairs of the walk's next round, loaded ahead (their
+  // latency then passes while warp 0 waits for the tile in between)
+  int64_t jw = 0;
+  int64_t pe[2], pb[2];
+  auto prefetch = [&]() {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t jj = jw + 32 * h + lane;
+      pe[h] = INT64_MAX;
+      pb[h] = 0;
+      if (jj < nmsg) {
+        pb[h] = __ldg(ms.in_off + jj);
+        pe[h] = __ldg(ms.in_off + jj + 1);
+      }
+    }
+  };
+  if (warp == 0) {
+    jw = first_end_after(ms.in_off, nmsg, tb * (int64_t)kFlatTile, lane);
+    prefetch();
+  }
+  // by all of warp 0: lane 0 issues tile t's copy, then the warp marks the
+  // final quads of the messages that end in the tile (two rounds of 32
+  // messages per step) while the copy is in flight, and lane 0 arrives a
+  // second time, which publishes the mask and the tile's place
+  auto issue = [&](int64_t t, uint32_t s) {
+    const int64_t T0 = t * (int64_t)kFlatTile;
+    const uint32_t len = (uint32_t)tmin<int64_t>(kFlatTile, M - T0);
+    const int64_t T1 = T0 + len;
+    const bool stall = wt.stall && blockIdx.x == 0 && t == tb;  // test: no copy, no arrivals
+    if (lane == 0 && !stall) {
+      const uint32_t bytes = len & ~15u;
+      if (bytes) {
+        fence_proxy_async_smem();  // earlier generic reads of this stage come first
+        mbar_arrive_expect_tx(&full[s], bytes);
+        tma_load_1d(smem + (size_t)s * kFlatTile, ms.src + T0, bytes, &full[s]);
+      } else {
+        mbar_arrive(&full[s]);
+      }
+    }
+    for (uint32_t i = lane; i < kFlatMaskWords; i += 32) fmask[s][i] = 0u;
+    __syncwarp();
+    const int64_t j_lo = jw;
+    for (;;) {  // pe, pb hold the round's offsets (for messages jw ..)
+      int n = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool inside = pe[h] <= T1;
+        if (inside && pe[h] > pb[h]) {
+          const uint32_t qi = (uint32_t)(pe[h] - 4 - T0) >> 2;
+          atomicOr(&fmask[s][qi >> 5], 1u << (qi & 31u));
+        }
+        n += __popc(__ballot_sync(0xFFFFFFFFu, inside));
+      }
+      jw += n;
+      prefetch();  // the next round's, or the next tile's first round
+      if (n < 64) break;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      meta[s] = FlatTile{T0, j_lo, len};
+      if (!stall) mbar_arrive(&full[s]);
+    }
+  };
+  if (warp == 0) {
+    fence_proxy_async_smem();
+    for (uint32_t s = 0; s < kFlatStages && tb + s < te; ++s) issue(tb + s, s);
+  }
+
+  bool timed_out = false;
+  uint32_t k = 0;
+  for (int64_t t = tb; t < te; ++t, ++k) {
+    const uint32_t s = k % kFlatStages;
+    const bool ok = mbar_wait_bounded(&full[s], (k / kFlatStages) & 1u, wt.limit_ns);
+    uint32_t* ob = reinterpret_cast<uint32_t*>(outbuf0 + (size_t)(k & 1u) * kFlatOut);
+    const FlatTile fm = meta[s];
+    const uint32_t nu = fm.len / 16u;
+    if (ok && warp != 0) {
+      const uint4* in = reinterpret_cast<const uint4*>(smem + (size_t)s * kFlatTile);
+#pragma unroll 4
+      for (uint32_t u = tid - 32u; u < nu; u += NT - 32) {
+        const uint4 v = in[u];
+        uint32_t err = 0;
+        const uint3 o = dec_unit(v, D, err);
+        ob[3 * u] = o.x;
+        ob[3 * u + 1] = o.y;
+        ob[3 * u + 2] = o.z;
+        if (err & kBadFlag)
+          flat_flagged(v, 4u * u, fmask[s], fm.T0, fm.j_lo, ms.in_off, nmsg, first_bad, D);
+      }
+      // whole quads after the last unit (the last tile of the batch only)
+      const uint32_t nq = (fm.len - 16u * nu) / 4u;
+      if (tid - 32u < nq) {
+        const uint32_t qi = 4u * nu + (tid - 32u);
+        const int64_t p = fm.T0 + 4 * (int64_t)qi;
+        const uint32_t x = *reinterpret_cast<const uint32_t*>(ms.src + p);
+        uint32_t err = 0;
+        const uint32_t val = dec_quad(x, D, err);
+        if (!(err & kBadFlag)) {
+          uint8_t* w = ms.dst + p / 4 * 3;
+          w[0] = (uint8_t)(val >> 16);
+          w[1] = (uint8_t)(val >> 8);
+          w[2] = (uint8_t)val;
+        } else {
+          flat_flagged(make_uint4(x, 0x41414141u, 0x41414141u, 0x41414141u), qi, fmask[s],
+                       fm.T0, fm.j_lo, ms.in_off, nmsg, first_bad, D);
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    if (tid == 0) bulk_wait_read_all();  // the other output buffer is free again
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      if (tid == 0) {  // wait (bounded) for this CTA's copies in flight
+        for (uint32_t jx = 0; jx < kFlatStages; ++jx) {
+          const uint32_t kk = k + jx;
+          const int64_t tt = t + jx;
+          if (tt < te && !(wt.stall && blockIdx.x == 0 && tt == tb))
+            mbar_wait_bounded(&full[kk % kFlatStages], (kk / kFlatStages) & 1u, 500000000ull);
+        }
+      }
+      break;
+    }
+    if (warp == 0) {
+      if (lane == 0) {
+        const uint32_t ob_bytes = 12u * nu;
+        const uint32_t sb = ob_bytes & ~15u;
+        uint8_t* gout = ms.dst + fm.T0 / 4 * 3;
+        if (sb) {
+          tma_store_1d(gout, ob, sb);
+          bulk_commit();
+        }
+        const uint8_t* obb = reinterpret_cast<const uint8_t*>(ob);
+        for (uint32_t i = sb; i < ob_bytes; ++i) gout[i] = obb[i];
+      }
+      const int64_t t2 = t + kFlatStages;
+      if (t2 < te) issue(t2, s);
+    }
+  }
+  if (tid == 0) {
+    bulk_wait_all();
+    if (timed_out) atomicOr(&g_batch_fault, 1u);
+  }
+}
+
 // Per-message status: first bad character wins, then the length rule, then
 // Appendix A's check (decoder of the final group returned a negative code).
 // While the fault word is set (a tile kernel gave up on a bounded wait, and
 // b64_device_fault has not cleared it since), every message reports
 // B64_ERR_TIMEOUT: some of them were never decoded.
+// after_flat: k_batch_flat ran before; for a batch it decoded, the final
+// group of each message is decoded here (its bytes written, its rules
+// checked).
 template <class Msgs>
 __global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restrict__ status,
                                       int64_t* __restrict__ first_bad,
-                                      int64_t* __restrict__ outlen, uint32_t flags) {
+                                      int64_t* __restrict__ outlen, uint32_t flags,
+                                      uint32_t after_flat) {
+  __shared__ uint8_t D[256];
+  const bool flat = after_flat && flat_batch(msgs, nmsg);
+  if (flat) {
+    init_tables(nullptr, D, flags & kFlagUrl);
+    __syncthreads();
+  }
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nmsg) return;
   const uint64_t m = (uint64_t)max((long long)0, (long long)msgs.len(j));
@@ -1076,7 +1360,12 @@ __global__ void k_batch_decode_finish(Msgs msgs, int64_t nmsg, int32_t* __restri
     return;
   }
   const uint64_t body_end = decode_body_end(m);
-  const int64_t final = (body_end < m) ? outlen[j] : 0;
+  int64_t final = (body_end < m) ? outlen[j] : 0;
+  if (flat && m > 0) {
+    const Msg g = msgs.get(j);
+    final = dec_final_group(g.src, m, body_end, g.out, D,
+                            reinterpret_cast<unsigned long long*>(first_bad + j), flags);
+  }
   const FinalStatus f = final_status(m, body_end, (unsigned long long)first_bad[j], final, flags);
   status[j] = f.status;
   first_bad[j] = f.first_bad;
@@ -1094,7 +1383,7 @@ __global__ void k_batch_decode_init(int64_t nmsg, int64_t* __restrict__ first_ba
 
 // ------------------------------------------------------------------ host
 size_t batch_smem_bytes(int decode, const BatchConfig& c) {
-  if (c.kernel == 2) return 0;  // unstaged tiles
+  if (c.kernel >= 2) return 0;  // unstaged tiles (and the flat decode's own kernel)
   return (size_t)(c.threads / 32) * warp_smem_bytes(decode, c.tile, (uint32_t)c.stages);
 }
 
@@ -1118,12 +1407,39 @@ cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
 }
 
 namespace {
+// The flat decode needs 16-byte aligned packed input and output (its bulk
+// copies); descriptor batches never take it.
+bool flat_possible(const PackedMsgs& m) {
+  return ((reinterpret_cast<uintptr_t>(m.src) | reinterpret_cast<uintptr_t>(m.dst)) & 15u) == 0;
+}
+bool flat_possible(const DescMsgs&) { return false; }
+
+// Launches k_batch_flat (one CTA per SM); it returns at once unless the
+// batch qualifies.
+cudaError_t launch_flat(const PackedMsgs& msgs, int64_t nmsg, int64_t* first_bad,
+                        const DeviceInfo* di, uint32_t flags, cudaStream_t stream) {
+  int fit = 0;
+  cudaError_t e = kernel_prepare(reinterpret_cast<const void*>(k_batch_flat), flat_smem_bytes(),
+                                 kFlatThreads, &fit);
+  if (e != cudaSuccess) return e;
+  if (fit < 1) return cudaErrorInvalidConfiguration;
+  k_batch_flat<<<di->sm_count, kFlatThreads, flat_smem_bytes(), stream>>>(msgs, nmsg, first_bad,
+                                                                          flags, wait_test());
+  return cudaGetLastError();
+}
+cudaError_t launch_flat(const DescMsgs&, int64_t, int64_t*, const DeviceInfo*, uint32_t,
+                        cudaStream_t) {
+  return cudaErrorInvalidValue;
+}
+
 template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* weight_off,
                         int32_t* status, int64_t* first_bad,
                         int64_t* outlen, const BatchConfig& cfg, const DeviceInfo* di,
                         uint32_t flags, cudaStream_t stream, int64_t small_max) {
-  const bool direct = cfg.kernel == 2;
+  // kernel 3: the flat decode when the batch qualifies, else the unstaged tiles
+  const bool flat = decode && cfg.kernel == 3 && flat_possible(msgs);
+  const bool direct = cfg.kernel >= 2;
   const size_t smem = batch_smem_bytes(decode, cfg);
   const void* kernel;
   if (direct) {
@@ -1142,13 +1458,17 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const uint32_t stages = (uint32_t)cfg.stages;
   const TileShape ts{cfg.tile, out_tile_bytes(decode, cfg.tile), small_max, DivBy::of(cfg.tile),
                      DivBy::of(cfg.tile + kTileCost)};
+  if (flat) {
+    e = launch_flat(msgs, nmsg, first_bad, di, flags, stream);
+    if (e != cudaSuccess) return e;
+  }
   if (direct) {
     if (decode) {
       k_batch_direct<NT, 1, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, weight_off, ts, first_bad,
-                                                           outlen, flags);
+                                                           outlen, flags, flat ? 1u : 0u);
     } else {
       k_batch_direct<NT, 0, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, weight_off, ts, nullptr,
-                                                           nullptr, flags);
+                                                           nullptr, flags, 0u);
     }
   } else if (decode) {
     k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,
@@ -1161,7 +1481,7 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   if (e != cudaSuccess || !decode) return e;
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
   k_batch_decode_finish<Msgs><<<(unsigned)blocks, 256, 0, stream>>>(msgs, nmsg, status, first_bad,
-                                                                   outlen, flags);
+                                                                   outlen, flags, flat ? 1u : 0u);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,9 @@ struct BatchConfig {
   int kernel = 0;     // 0 = short messages one thread each (packed batches)
                       // and staged per-warp tiles for the rest, 1 = staged
                       // tiles for every message, 2 = short messages one
-                      // thread each and unstaged tiles (up to 64 rows)
+                      // thread each and unstaged tiles (up to 64 rows),
+                      // 3 = (decode) the flat decode of a packed batch whose
+                      // lengths are all multiples of 4, else as 2
 };
 
 struct BatchArgs {

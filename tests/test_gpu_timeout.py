@@ -138,3 +138,26 @@ def test_whitespace_decode_times_out_then_recovers(gb64, oracle):
     assert np.array_equal(dst[:raw.size].cpu().numpy(), raw)
     ost, oout, ofb = oracle.decode_ex(s, 8)
     assert (ost, ofb) == (0, len(s)) and np.array_equal(oout, raw)
+
+
+def test_flat_batch_decode_times_out_then_recovers(gb64, oracle):
+    """The flat decode of a padded batch (the default decode of such
+    batches): CTA 0's first copy is left out, its wait runs out, every
+    message reports B64_ERR_TIMEOUT; then the batch decodes exactly."""
+    import torch
+
+    data, off = W.batched(nmsg=3000, seed=45, median=6000.0, sigma=1.0)
+    src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
+    benc, boff = gb64.b64_encode_batch(src, doff)
+    with stalled(gb64):
+        _, _, st, fb, ol = gb64.b64_decode_batch(benc, boff)
+        torch.cuda.synchronize()
+        assert bool((st == gb64.B64_ERR_TIMEOUT).all())
+        assert gb64.b64_device_fault() == gb64.B64_ERR_TIMEOUT
+    ddst, doff2, st, fb, ol = gb64.b64_decode_batch(benc, boff)
+    assert int((st != 0).sum()) == 0
+    assert np.array_equal(ol.cpu().numpy(), np.diff(off))
+    h, oo = ddst.cpu().numpy(), doff2.cpu().numpy()
+    for j in range(0, off.size - 1, 29):
+        assert np.array_equal(h[oo[j]:oo[j] + off[j + 1] - off[j]], data[off[j]:off[j + 1]])
+    assert gb64.b64_device_fault() == 0
