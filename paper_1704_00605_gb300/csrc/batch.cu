@@ -1045,7 +1045,7 @@ __global__ void __launch_bounds__(NT)
                    uint32_t after_flat) {
   __shared__ uint8_t table[DECODE ? 256 : 64];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  if (DECODE && after_flat && flat_batch(msgs, nmsg)) return;
+  if (after_flat && (DECODE ? flat_batch(msgs, nmsg) : flat_enc_batch(msgs, nmsg))) return;
   if (DECODE) {
     init_tables(nullptr, table, flags & kFlagUrl);
   } else {
@@ -1102,6 +1102,20 @@ constexpr uint32_t kFlatMaskWords = kFlatTile / 4u / 32u;  // one bit per quad
 
 __host__ __device__ constexpr size_t flat_smem_bytes() {
   return (size_t)kFlatStages * kFlatTile + 2 * (size_t)kFlatOut;
+}
+
+// Whether a packed encode batch takes the flat encode (k_batch_flat_enc:
+// padded output, so every message's characters start on a quad, and a mean
+// output length of at least kFlatMinMean characters; the host checks the
+// flags and the alignments); k_batch_flat_enc and the tile walk decide
+// alike.
+template <class Msgs>
+__device__ __forceinline__ bool flat_enc_batch(const Msgs&, int64_t) {
+  return false;
+}
+template <>
+__device__ __forceinline__ bool flat_enc_batch<PackedMsgs>(const PackedMsgs& ms, int64_t nmsg) {
+  return nmsg > 0 && __ldg(ms.out_off + nmsg) >= kFlatMinMean * nmsg;
 }
 
 // The first message j whose end in_off[j + 1] exceeds x (x < in_off[nmsg]),
@@ -1265,16 +1279,26 @@ __global__ void __launch_bounds__(kFlatThreads, 1)
     const uint32_t nu = fm.len / 16u;
     if (ok && warp != 0) {
       const uint4* in = reinterpret_cast<const uint4*>(smem + (size_t)s * kFlatTile);
-#pragma unroll 4
-      for (uint32_t u = tid - 32u; u < nu; u += NT - 32) {
-        const uint4 v = in[u];
-        uint32_t err = 0;
-        const uint3 o = dec_unit(v, D, err);
-        ob[3 * u] = o.x;
-        ob[3 * u + 1] = o.y;
-        ob[3 * u + 2] = o.z;
-        if (err & kBadFlag)
-          flat_flagged(v, 4u * u, fmask[s], fm.T0, fm.j_lo, ms.in_off, nmsg, first_bad, D);
+      // flagged units (mostly padded final quads) are looked at after the
+      // loop, which then has no call in it
+      uint32_t flagged = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < kFlatUnits; ++i) {
+        const uint32_t u = tid - 32u + (NT - 32) * i;
+        if (u < nu) {
+          uint32_t err = 0;
+          const uint3 o = dec_unit(in[u], D, err);
+          ob[3 * u] = o.x;
+          ob[3 * u + 1] = o.y;
+          ob[3 * u + 2] = o.z;
+          if (err & kBadFlag) flagged |= 1u << i;
+        }
+      }
+      while (flagged) {
+        const uint32_t i = __ffs(flagged) - 1;
+        flagged &= flagged - 1;
+        const uint32_t u = tid - 32u + (NT - 32) * i;
+        flat_flagged(in[u], 4u * u, fmask[s], fm.T0, fm.j_lo, ms.in_off, nmsg, first_bad, D);
       }
       // whole quads after the last unit (the last tile of the batch only)
       const uint32_t nq = (fm.len - 16u * nu) / 4u;
@@ -1322,6 +1346,337 @@ __global__ void __launch_bounds__(kFlatThreads, 1)
         for (uint32_t i = sb; i < ob_bytes; ++i) gout[i] = obb[i];
       }
       const int64_t t2 = t + kFlatStages;
+      if (t2 < te) issue(t2, s);
+    }
+  }
+  if (tid == 0) {
+    bulk_wait_all();
+    if (timed_out) atomicOr(&g_batch_fault, 1u);
+  }
+}
+
+// ------------------------------------------------------------ flat encode
+// The same idea for encoding. With padding, message j's characters start
+// on a quad (out_off[j] = 4 qs_j) and quad q of it encodes input bytes
+// 3 q + d_j (d_j = in_off[j] - 3 qs_j): so the batch's output is one flat
+// sequence of quads, and the input of an output tile is one contiguous
+// range. Each CTA takes a contiguous run of output tiles of 53,760
+// characters; warp 0 stages each tile's input range by TMA and lists in a
+// segment table beside it the messages that overlap the tile (first and
+// end quad, shift, bytes of the last group); the other warps encode
+// 16-character units, a unit inside one message, short of its last quad,
+// from 12 staged bytes (Algorithm 1's main loop), any other unit quad by
+// quad with the message's last group padded (Algorithm 1's tail). The
+// characters go straight to global memory in aligned 16-byte stores (the
+// tile's output starts on 16 bytes), four tiles' input staged ahead.
+constexpr uint32_t kFlatEncUnits = 7;
+constexpr uint32_t kFlatEncTile = (uint32_t)(kFlatThreads - 32) * kFlatEncUnits * 16u;  // 53,760
+constexpr uint32_t kFlatEncQuads = kFlatEncTile / 4u;
+// a tile's input, at most 3 bytes per quad, after up to 15 bytes of alignment
+// and before the 16 bytes a unit's word reads may pass its last byte
+constexpr uint32_t kFlatEncStage = (kFlatEncQuads * 3u + 32u + 127u) & ~127u;
+constexpr uint32_t kFlatMaxSegs = 512;
+constexpr uint32_t kFlatEncStages = 4;
+
+__host__ __device__ constexpr size_t flat_enc_smem_bytes() {
+  return (size_t)kFlatEncStages * kFlatEncStage +
+         (size_t)kFlatEncStages * kFlatMaxSegs * sizeof(int4);
+}
+
+// One message as a tile sees it: quads [qs, qe) relative to the tile's
+// first quad, stage position 3 q + sd of quad q's first byte, and the
+// bytes of its last group (1..3).
+__device__ __forceinline__ int4 flat_seg(int32_t qs, int32_t qe, int32_t sd, int32_t last) {
+  return make_int4(qs, qe, sd, last);
+}
+
+// A tile's place beside its stage (written by warp 0 before the arrive that
+// publishes it).
+struct FlatEncTile {
+  int64_t Q0;      // first quad
+  int64_t G;       // input offset of stage byte 0 (16-byte aligned)
+  int64_t j_cut;   // first message not in the segment table (nmsg: none)
+  uint32_t nq;     // quads
+  uint32_t nseg;   // segments listed
+  uint32_t ia, ib; // staged bytes
+};
+
+// The message of quad q (absolute) among [lo, nmsg): quads of message j are
+// [out_off[j] / 4, out_off[j + 1] / 4).
+__device__ __forceinline__ int64_t flat_msg_of_quad(const int64_t* out_off, int64_t nmsg,
+                                                    int64_t lo, int64_t q) {
+  int64_t hi = nmsg - 1;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (__ldg(out_off + mid + 1) > 4 * q) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Quads [q0, q1) of a tile (relative), one at a time: the message's shift
+// from the segment table (or, past the table's cut, from the offsets), its
+// bytes from the stage when staged, else from global memory, encoded with
+// the tail rule of its last group; the characters to ob (the tile's output).
+__device__ __noinline__ void flat_enc_quads(const FlatEncTile fm, const int4* segs, uint32_t k,
+                                            uint32_t q0, uint32_t q1, const uint8_t* st,
+                                            const PackedMsgs ms, int64_t nmsg, uint32_t* ob,
+                                            const uint8_t* T) {
+  for (uint32_t q = q0; q < q1; ++q) {
+    int64_t in;
+    uint32_t cnt = 3;
+    const int64_t qa = fm.Q0 + q;
+    int4 sg = make_int4(0, 0, 0, 0);
+    bool found = false;
+    while (k < fm.nseg) {
+      sg = segs[k];
+      if ((uint32_t)sg.y > q) {
+        found = (uint32_t)max(sg.x, 0) <= q;
+        break;
+      }
+      ++k;
+    }
+    if (found) {
+      in = fm.G + 3 * (int64_t)q + sg.z;
+      if (q + 1 == (uint32_t)sg.y) cnt = (uint32_t)sg.w;
+    } else {  // past the table's cut: the offsets
+      const int64_t j = flat_msg_of_quad(ms.out_off, nmsg, fm.j_cut, qa);
+      const int64_t qs = __ldg(ms.out_off + j) / 4, qe = __ldg(ms.out_off + j + 1) / 4;
+      const int64_t i0 = __ldg(ms.in_off + j), n = __ldg(ms.in_off + j + 1) - i0;
+      in = i0 + 3 * (qa - qs);
+      if (qa + 1 == qe) cnt = (uint32_t)(n - 3 * (qe - 1 - qs));
+    }
+    uint32_t b[3] = {0, 0, 0};
+    const int64_t sp = in - fm.G;
+    for (uint32_t i = 0; i < cnt; ++i) {
+      const int64_t x = sp + i;
+      b[i] = (x >= fm.ia && x < fm.ib) ? st[x] : ms.src[in + i];
+    }
+    ob[q] = enc_tail_group(b[0], b[1], b[2], cnt, T);
+  }
+}
+
+__global__ void __launch_bounds__(kFlatThreads, 1)
+    k_batch_flat_enc(PackedMsgs ms, int64_t nmsg, uint32_t flags, WaitTest wt) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint8_t T[64];
+  __shared__ __align__(8) uint64_t full[kFlatEncStages];
+  __shared__ FlatEncTile meta[kFlatEncStages];
+  // per stage and row of 32 units: the segment of the row's first quad, and
+  // the row's shift when the whole row is one message's, short of its last
+  // quad, and staged (kNotSimple otherwise)
+  __shared__ uint16_t rowseg[kFlatEncStages][kFlatEncQuads / 128u];
+  __shared__ int32_t rowsd[kFlatEncStages][kFlatEncQuads / 128u];
+  constexpr int32_t kNotSimple = INT32_MIN;
+  constexpr int NT = kFlatThreads;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  if (!flat_enc_batch(ms, nmsg)) return;  // the tile walk encodes the batch
+  if (tid == 0) {  // two arrivals per phase: the copy's (with its bytes), then the table's
+    for (uint32_t s = 0; s < kFlatEncStages; ++s) mbar_init(&full[s], 2);
+    fence_mbar_init();
+  }
+  init_tables(T, nullptr, flags & kFlagUrl);
+  __syncthreads();
+  const int64_t N = __ldg(ms.in_off + nmsg);   // input bytes
+  const int64_t NQ = __ldg(ms.out_off + nmsg) / 4;  // output quads
+  const int64_t ntiles = (NQ + kFlatEncQuads - 1) / kFlatEncQuads;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t tb = tmin<int64_t>(ntiles, (int64_t)blockIdx.x * per);
+  const int64_t te = tmin<int64_t>(ntiles, tb + per);
+  if (tb >= te) return;
+  int4* segs0 = reinterpret_cast<int4*>(smem + (size_t)kFlatEncStages * kFlatEncStage);
+
+  // warp 0: the first message whose quads reach past the next tile's start,
+  // and the lane's two messages of the walk's next round, loaded ahead
+  int64_t jw = 0;
+  int64_t pqs[2], pqe[2], pin[2], pn[2];
+  auto prefetch = [&]() {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t jj = jw + 32 * h + lane;
+      pqs[h] = pqe[h] = INT64_MAX;
+      pin[h] = pn[h] = 0;
+      if (jj < nmsg) {
+        pqs[h] = __ldg(ms.out_off + jj) / 4;
+        pqe[h] = __ldg(ms.out_off + jj + 1) / 4;
+        pin[h] = __ldg(ms.in_off + jj);
+        pn[h] = __ldg(ms.in_off + jj + 1) - pin[h];
+      }
+    }
+  };
+  if (warp == 0) {
+    jw = first_end_after(ms.out_off, nmsg, 4 * tb * (int64_t)kFlatEncQuads, lane);
+    prefetch();
+  }
+  // by all of warp 0: the tile's input range (from its first quad's
+  // message), lane 0's copy of it, then the segment table while the copy
+  // is in flight, and lane 0's second arrival
+  auto issue = [&](int64_t t, uint32_t s) {
+    const int64_t Q0 = t * (int64_t)kFlatEncQuads;
+    const uint32_t nq = (uint32_t)tmin<int64_t>(kFlatEncQuads, NQ - Q0);
+    const int64_t Q1 = Q0 + nq;
+    // message jw holds quad Q0 (lane 0's prefetched values)
+    const int64_t qs0 = __shfl_sync(0xFFFFFFFFu, pqs[0], 0);
+    const int64_t in0 = __shfl_sync(0xFFFFFFFFu, pin[0], 0);
+    const int64_t inQ0 = in0 + 3 * (Q0 - qs0);
+    const int64_t G = inQ0 & ~(int64_t)15;
+    const int64_t hi = tmin<int64_t>((inQ0 + 3 * (int64_t)nq + 15) & ~(int64_t)15, N & ~(int64_t)15);
+    const uint32_t ib = hi > G ? (uint32_t)(hi - G) : 0u;
+    const bool stall = wt.stall && blockIdx.x == 0 && t == tb;  // test: no copy, no arrivals
+    if (lane == 0 && !stall) {
+      if (ib) {
+        fence_proxy_async_smem();  // earlier generic reads of this stage come first
+        mbar_arrive_expect_tx(&full[s], ib);
+        tma_load_1d(smem + (size_t)s * kFlatEncStage, ms.src + G, ib, &full[s]);
+      } else {
+        mbar_arrive(&full[s]);
+      }
+    }
+    int4* segs = segs0 + (size_t)s * kFlatMaxSegs;
+    uint32_t nseg = 0;
+    int64_t j_cut = nmsg;
+    for (;;) {  // pqs .. hold the round's messages (jw ..)
+      int n = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool take = pqs[h] < Q1 && pqe[h] > pqs[h];  // overlaps the tile, not empty
+        const uint32_t bt = __ballot_sync(0xFFFFFFFFu, take);
+        const uint32_t k = nseg + __popc(bt & ((1u << lane) - 1u));
+        if (take && k < kFlatMaxSegs) {
+          const int64_t qs = pqs[h] - Q0, qe = pqe[h] - Q0;
+          const int64_t sd = pin[h] - 3 * pqs[h] + 3 * Q0 - G;
+          const int32_t last = (int32_t)(pn[h] - 3 * (pqe[h] - 1 - pqs[h]));
+          segs[k] = flat_seg((int32_t)tmax<int64_t>(qs, -1), (int32_t)tmin<int64_t>(qe, nq + 1),
+                             (int32_t)sd, last);
+        }
+        const uint32_t cb = __ballot_sync(0xFFFFFFFFu, take && k == kFlatMaxSegs);
+        if (cb && j_cut == nmsg) j_cut = jw + 32 * h + (__ffs(cb) - 1);  // (warp-uniform)
+        nseg += __popc(bt);
+        n += __popc(__ballot_sync(0xFFFFFFFFu, pqe[h] <= Q1));  // ends inside the tile
+      }
+      jw += n;
+      prefetch();  // the next round's, or the next tile's first round
+      if (n < 64) break;
+    }
+    __syncwarp();
+    const uint32_t nsg = min(nseg, kFlatMaxSegs);
+    for (uint32_t r = lane; r < (nq + 127u) / 128u; r += 32) {
+      uint32_t lo = 0, hi = nsg;  // the last segment starting at or before quad 128 r
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (segs[mid].x <= (int32_t)(128u * r)) lo = mid; else hi = mid;
+      }
+      rowseg[s][r] = (uint16_t)lo;
+      const int4 g = segs[lo];
+      const uint32_t qa = 128u * r, qb = qa + 128u;  // the row's quads
+      const bool simple = nsg > 0 && g.x <= (int32_t)qa && (int32_t)qb < g.y && qb <= nq &&
+                          ((3u * (qb - 4u) + (uint32_t)g.z) & ~3u) + 16u <= ib &&
+                          (int64_t)3 * qa + g.z >= 0;
+      rowsd[s][r] = simple ? g.z : kNotSimple;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      meta[s] = FlatEncTile{Q0, G, j_cut, nq, nsg, 0u, ib};
+      if (!stall) mbar_arrive(&full[s]);
+    }
+  };
+  if (warp == 0) {
+    fence_proxy_async_smem();
+    for (uint32_t s = 0; s < kFlatEncStages && tb + s < te; ++s) issue(tb + s, s);
+  }
+
+  bool timed_out = false;
+  uint32_t k = 0;
+  for (int64_t t = tb; t < te; ++t, ++k) {
+    const uint32_t s = k % kFlatEncStages;
+    const bool ok = mbar_wait_bounded(&full[s], (k / kFlatEncStages) & 1u, wt.limit_ns);
+    const FlatEncTile fm = meta[s];
+    uint32_t* ob = reinterpret_cast<uint32_t*>(ms.dst + 4 * fm.Q0);  // the tile's output
+    if (ok && warp != 0) {
+      const uint8_t* st = smem + (size_t)s * kFlatEncStage;
+      const int4* segs = segs0 + (size_t)s * kFlatMaxSegs;
+      const uint16_t* rows = rowseg[s];
+      const uint32_t nu = (fm.nq + 3u) / 4u;
+      // every unit by the main loop's rule (12 staged bytes of one message:
+      // its segment from the row table, then at most a step or two), with
+      // no branch on the outcome, so that the units' loads overlap; the few
+      // units that rule does not fit (a message end or start inside, an
+      // unstaged range) are marked and done again quad by quad
+      uint32_t redo = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < kFlatEncUnits; ++i) {
+        const uint32_t u = tid - 32u + (NT - 32) * i;
+        // a warp's 32 units of a step form one row (480 = 15 rows)
+        const int32_t rsd = u < nu ? rowsd[s][u >> 5] : kNotSimple;
+        if (rsd != kNotSimple) {  // one message's row: the main loop alone
+          const uint32_t sp = 12u * u + (uint32_t)rsd;
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(st + (sp & ~3u));
+          const uint32_t sh = 8u * (sp & 3u);
+          const uint32_t x0 = w[0], x1 = w[1], x2 = w[2], x3 = w[3];
+          st_global_v4_cs(reinterpret_cast<uint8_t*>(ob) + 16u * u,
+                          enc_unit(__funnelshift_r(x0, x1, sh), __funnelshift_r(x1, x2, sh),
+                                   __funnelshift_r(x2, x3, sh), T));
+        } else if (u < nu) {
+          const uint32_t q = 4u * u;
+          uint32_t k = rows[u >> 5];
+          while (k + 1 < fm.nseg && segs[k + 1].x <= (int32_t)q) ++k;
+          const int4 sg = segs[k];
+          const uint32_t sp = 3u * q + (uint32_t)sg.z;
+          const uint32_t a = min(sp & ~3u, kFlatEncStage - 16u);  // (stays in the stage)
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(st + a);
+          const uint32_t sh = 8u * (sp & 3u);
+          const uint32_t x0 = w[0], x1 = w[1], x2 = w[2], x3 = w[3];
+          const uint4 o = enc_unit(__funnelshift_r(x0, x1, sh), __funnelshift_r(x1, x2, sh),
+                                   __funnelshift_r(x2, x3, sh), T);
+          const bool fits = sg.x <= (int32_t)q && (int32_t)q + 4 < sg.y && q + 4u <= fm.nq &&
+                            (sp & ~3u) + 16u <= fm.ib;
+          if (fits) st_global_v4_cs(reinterpret_cast<uint8_t*>(ob) + 16u * u, o);
+          else redo |= 1u << i;
+        }
+      }
+      while (redo) {  // quad by quad: each in its message, the last group padded
+        const uint32_t i = __ffs(redo) - 1;
+        redo &= redo - 1;
+        const uint32_t u = tid - 32u + (NT - 32) * i;
+        const uint32_t q = 4u * u;
+        uint32_t kq = rows[u >> 5];
+        for (uint32_t e = 0; e < 4; ++e) {
+          const uint32_t qq = q + e;
+          if (qq >= fm.nq) break;
+          while (kq + 1 < fm.nseg && segs[kq].y <= (int32_t)qq) ++kq;
+          const int4 g = segs[kq];
+          const uint32_t gp = 3u * qq + (uint32_t)g.z;
+          const uint32_t ga = gp & ~3u;
+          if (g.x > (int32_t)qq || g.y <= (int32_t)qq || ga + 8u > fm.ib) {
+            flat_enc_quads(fm, segs, kq, qq, qq + 1, st, ms, nmsg, ob, T);  // rare
+            continue;
+          }
+          const uint32_t cnt = qq + 1 == (uint32_t)g.y ? (uint32_t)g.w : 3u;
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(st + ga);
+          uint32_t x = __funnelshift_r(w[0], w[1], 8u * (gp & 3u));
+          x &= cnt == 1 ? 0xFFu : cnt == 2 ? 0xFFFFu : 0xFFFFFFu;
+          uint32_t c4 = enc_group(__byte_perm(x, 0u, 0x4012), T);
+          if (cnt == 1) c4 = (c4 & 0x0000FFFFu) | (kPadChar << 16) | (kPadChar << 24);
+          if (cnt == 2) c4 = (c4 & 0x00FFFFFFu) | (kPadChar << 24);
+          ob[qq] = c4;
+        }
+      }
+    }
+    fence_proxy_async_smem();  // this stage's reads come before its next copy
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      if (tid == 0) {  // wait (bounded) for this CTA's copies in flight
+        for (uint32_t jx = 0; jx < kFlatEncStages; ++jx) {
+          const uint32_t kk = k + jx;
+          const int64_t tt = t + jx;
+          if (tt < te && !(wt.stall && blockIdx.x == 0 && tt == tb))
+            mbar_wait_bounded(&full[kk % kFlatEncStages], (kk / kFlatEncStages) & 1u,
+                              500000000ull);
+        }
+      }
+      break;
+    }
+    if (warp == 0) {
+      const int64_t t2 = t + kFlatEncStages;
       if (t2 < te) issue(t2, s);
     }
   }
@@ -1432,13 +1787,32 @@ cudaError_t launch_flat(const DescMsgs&, int64_t, int64_t*, const DeviceInfo*, u
   return cudaErrorInvalidValue;
 }
 
+// Launches k_batch_flat_enc (one CTA per SM); it returns at once unless the
+// batch qualifies.
+cudaError_t launch_flat_enc(const PackedMsgs& msgs, int64_t nmsg, const DeviceInfo* di,
+                            uint32_t flags, cudaStream_t stream) {
+  int fit = 0;
+  cudaError_t e = kernel_prepare(reinterpret_cast<const void*>(k_batch_flat_enc),
+                                 flat_enc_smem_bytes(), kFlatThreads, &fit);
+  if (e != cudaSuccess) return e;
+  if (fit < 1) return cudaErrorInvalidConfiguration;
+  k_batch_flat_enc<<<di->sm_count, kFlatThreads, flat_enc_smem_bytes(), stream>>>(
+      msgs, nmsg, flags, wait_test());
+  return cudaGetLastError();
+}
+cudaError_t launch_flat_enc(const DescMsgs&, int64_t, const DeviceInfo*, uint32_t, cudaStream_t) {
+  return cudaErrorInvalidValue;
+}
+
 template <int NT, class Msgs>
 cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_t* weight_off,
                         int32_t* status, int64_t* first_bad,
                         int64_t* outlen, const BatchConfig& cfg, const DeviceInfo* di,
                         uint32_t flags, cudaStream_t stream, int64_t small_max) {
-  // kernel 3: the flat decode when the batch qualifies, else the unstaged tiles
-  const bool flat = decode && cfg.kernel == 3 && flat_possible(msgs);
+  // kernel 3: the flat decode or encode when the batch qualifies (padded
+  // output, for encode), else the unstaged tiles
+  const bool flat =
+      cfg.kernel == 3 && flat_possible(msgs) && (decode || !(flags & kFlagNoPad));
   const bool direct = cfg.kernel >= 2;
   const size_t smem = batch_smem_bytes(decode, cfg);
   const void* kernel;
@@ -1459,7 +1833,8 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
   const TileShape ts{cfg.tile, out_tile_bytes(decode, cfg.tile), small_max, DivBy::of(cfg.tile),
                      DivBy::of(cfg.tile + kTileCost)};
   if (flat) {
-    e = launch_flat(msgs, nmsg, first_bad, di, flags, stream);
+    e = decode ? launch_flat(msgs, nmsg, first_bad, di, flags, stream)
+               : launch_flat_enc(msgs, nmsg, di, flags, stream);
     if (e != cudaSuccess) return e;
   }
   if (direct) {
@@ -1468,7 +1843,7 @@ cudaError_t launch_work(int decode, const Msgs& msgs, int64_t nmsg, const int64_
                                                            outlen, flags, flat ? 1u : 0u);
     } else {
       k_batch_direct<NT, 0, Msgs><<<grid, NT, 0, stream>>>(msgs, nmsg, weight_off, ts, nullptr,
-                                                           nullptr, flags, 0u);
+                                                           nullptr, flags, flat ? 1u : 0u);
     }
   } else if (decode) {
     k_batch_code<NT, 1, Msgs><<<grid, NT, smem, stream>>>(msgs, nmsg, weight_off, ts, stages,

@@ -19,8 +19,9 @@ struct BatchConfig {
                       // and staged per-warp tiles for the rest, 1 = staged
                       // tiles for every message, 2 = short messages one
                       // thread each and unstaged tiles (up to 64 rows),
-                      // 3 = (decode) the flat decode of a packed batch whose
-                      // lengths are all multiples of 4, else as 2
+                      // 3 = the flat decode (encode) of a packed batch whose
+                      // encoded lengths are all multiples of 4 (padded
+                      // output), else as 2
 };
 
 struct BatchArgs {

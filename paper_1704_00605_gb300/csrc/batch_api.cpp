@@ -12,7 +12,7 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
   if (c.threads != 128 && c.threads != 256 && c.threads != 512) return false;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) return false;
   if (c.stages < 2 || c.stages > 6) return false;
-  if (c.kernel < 0 || c.kernel > (decode ? 3 : 2)) return false;
+  if (c.kernel < 0 || c.kernel > 3) return false;
   const int64_t row = decode ? 512 : 384;  // one unit per lane of a warp
   const int64_t max_rows = c.kernel >= 2 ? 64 : 16;  // unstaged tiles need no shared memory
   if (c.tile < row || c.tile > max_rows * row || c.tile % row) return false;
@@ -24,13 +24,14 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
 // average, and 64 of 1 MiB). Decoding longer messages, unstaged tiles of 32
 // rows beat staged ones (a shared-memory output buffer and its bulk store
 // per tile, and tiles limited to 8 rows); encoding, the two are even and
-// staged tiles stay. Decoding, the flat decode (kernel 3) takes every padded
-// batch of messages of at least 1 Ki characters on average and leaves the
-// rest to those unstaged tiles. mean_len < 0: unknown.
+// staged tiles stay. The flat kernels (kernel 3) take every batch of
+// messages of at least 1 Ki characters on average (padded, and with
+// aligned buffers) and leave the rest to the unstaged tiles. mean_len < 0:
+// unknown.
 BatchConfig default_batch_config(int decode, int64_t mean_len) {
   const bool small = mean_len >= 0 && mean_len < 1024;
   if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 16384, 0, 2, 3};
-  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2};
+  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2, 3};
 }
 
 namespace {

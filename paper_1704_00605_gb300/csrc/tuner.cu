@@ -157,11 +157,10 @@ std::vector<b64_shape> batch_candidates(int decode) {
       const b64_shape s{threads, 2, 2, 0, row * rows, 0.f};
       if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
     }
-  if (decode)
-    for (int rows : {8, 32}) {  // the flat decode, unstaged tiles otherwise (choice 3)
-      const b64_shape s{128, 3, 2, 0, row * rows, 0.f};
-      if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
-    }
+  for (int rows : {8, 32}) {  // the flat kernels, unstaged tiles otherwise (choice 3)
+    const b64_shape s{decode ? 128 : 256, 3, 2, 0, row * rows, 0.f};
+    if (batch_config_valid(decode, batch_config_of(s))) out.push_back(s);
+  }
   return out;
 }
 

@@ -142,8 +142,10 @@ def test_shape_table_host_side(g, tmp_path):
     with pytest.raises(g.Gb64Error):  # staged tiles: at most 16 rows
         g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=128, tile=17 * 384,
                         units_per_thread=0)
-    with pytest.raises(g.Gb64Error):
-        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, units_per_thread=3)
+    with pytest.raises(g.Gb64Error):  # kernel choices are 0 .. 3
+        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, units_per_thread=4)
+    g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=256, tile=16 * 384, stages=2,
+                    units_per_thread=3)  # the flat encode, unstaged tiles otherwise
     g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=512, tile=1024, stages=2,
                     blocks_per_sm=4)
     assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["stages"] == 2

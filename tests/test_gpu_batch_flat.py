@@ -1,5 +1,6 @@
-"""The flat decode of packed batches (kernel choice 3, the default for
-decode): a batch whose encoded lengths are all multiples of 4 decodes as one
+"""The flat kernels of packed batches (kernel choice 3, the default).
+
+Decode: a batch whose encoded lengths are all multiples of 4 decodes as one
 buffer, the last quad of each message (its final group) decoded by the
 finish kernel. Exact against the oracle per message (status, first_bad,
 outlen, bytes) with errors in bodies, in final groups and on padding
@@ -7,7 +8,12 @@ positions, '=' inside a body, empty messages, messages that end on and
 next to tile boundaries, the decode flags; the same batches through the
 unstaged tiles agree; batches that do not qualify (a length not a multiple
 of 4, short messages on average, buffers off a 16-byte boundary) fall back
-to the tile walk and stay exact."""
+to the tile walk and stay exact.
+
+Encode: padded output is one flat sequence of quads; exact against the
+oracle with empty messages, tile-boundary lengths, a tile holding more
+messages than its segment table, the url alphabet, and the fallbacks
+(unpadded output, an unaligned output, short messages)."""
 import numpy as np
 import pytest
 
@@ -157,3 +163,85 @@ def test_flat_decode_large(gb64, oracle):
     for j in range(0, off.size - 1, 997):
         est, eout, efb = oracle.decode_ex(e[eo[j]:eo[j + 1]], 0)
         assert (est, efb) == (0, eo[j + 1] - eo[j]) and np.array_equal(eout, data[off[j]:off[j + 1]])
+
+
+def _enc_flat(gb64, data, off, flags=0, shift=0, kernel=3):
+    import torch
+
+    kind = gb64.B64_KIND_ENCODE_BATCH
+    saved = gb64.b64_shape_get(kind, -1, 1)
+    try:
+        gb64.b64_shape_set(kind, -1, 1, units_per_thread=kernel, threads=256, stages=2,
+                           tile=16 * 384)
+        doff = torch.from_numpy(np.ascontiguousarray(off)).cuda()
+        out_off = torch.empty(off.size, dtype=torch.int64, device="cuda")
+        gb64.b64_batch_out_offsets_ex(False, doff, flags, out_off)
+        need = int(out_off[-1].item())
+        buf = torch.zeros(need + 512, dtype=torch.uint8, device="cuda")
+        base = (-buf.data_ptr()) % 256
+        dst = buf[base + shift:base + shift + max(need, 1)]
+        gb64.b64_encode_batch_ex(_dev(data), doff, flags, dst=dst, out_off=out_off)
+        torch.cuda.synchronize()
+    finally:
+        gb64.b64_shape_set(kind, -1, 1, **{f: saved[f] for f in (
+            "threads", "units_per_thread", "stages", "blocks_per_sm", "tile")})
+    return dst.cpu().numpy()[:need], out_off.cpu().numpy()
+
+
+def _enc_lengths(seed, nmsg, mean=5000):
+    """Log-normal lengths (empty ones among them), lengths whose encodings
+    end on and next to the flat encode's tile boundary (53,760 characters),
+    and a run of a thousand tiny messages (more messages in one tile than
+    its segment table holds)."""
+    rng = np.random.default_rng(seed)
+    lens = np.maximum(0, rng.lognormal(np.log(mean), 1.0, nmsg)).astype(np.int64)
+    lens[rng.integers(0, nmsg, nmsg // 20)] = 0
+    at = 53760 // 4 * 3
+    lens[:6] = [at, at - 1, at + 1, at - 2, 2 * at, 3]
+    lens[100:1100] = rng.integers(0, 12, 1000)
+    return lens
+
+
+@pytest.mark.parametrize("flags", [0, URL])
+def test_flat_encode_exact(gb64, oracle, flags):
+    lens = _enc_lengths(40 + flags, 3000)
+    off = W.offsets_from_lengths(lens)
+    data = W.uniform_bytes(int(off[-1]), 41 + flags)
+    exp = np.concatenate([oracle.encode_ex(data[off[j]:off[j + 1]], flags)
+                          for j in range(off.size - 1)])
+    out, out_off = _enc_flat(gb64, data, off, flags)
+    assert np.array_equal(out_off, W.offsets_from_lengths(4 * ((lens + 2) // 3)))
+    assert np.array_equal(out, exp)
+    walk, _ = _enc_flat(gb64, data, off, flags, kernel=2)
+    assert np.array_equal(walk, exp)
+
+
+def test_flat_encode_fallbacks(gb64, oracle):
+    """Kernel choice 3 where the flat encode does not apply: unpadded output,
+    an output off a 16-byte boundary, short messages on average."""
+    lens = _enc_lengths(50, 1500)
+    off = W.offsets_from_lengths(lens)
+    data = W.uniform_bytes(int(off[-1]), 51)
+    nopad = np.concatenate([oracle.encode_ex(data[off[j]:off[j + 1]], NOPAD)
+                            for j in range(off.size - 1)])
+    assert np.array_equal(_enc_flat(gb64, data, off, NOPAD)[0], nopad)
+    exp, _ = oracle.encode_batch(data, off)
+    assert np.array_equal(_enc_flat(gb64, data, off, shift=4)[0], exp)
+    short = np.random.default_rng(52).integers(0, 200, 20_000).astype(np.int64)
+    soff = W.offsets_from_lengths(short)
+    sdata = W.uniform_bytes(int(soff[-1]), 53)
+    assert np.array_equal(_enc_flat(gb64, sdata, soff)[0], oracle.encode_batch(sdata, soff)[0])
+
+
+def test_flat_round_trip_large(gb64, oracle):
+    """The 100,000-message mix encoded and decoded by default (both flat):
+    the encoding equals the oracle's in full, the decode every message."""
+    import torch
+
+    data, off = W.batched()
+    exp, exp_off = oracle.encode_batch(data, off)
+    src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
+    enc, eoff = gb64.b64_encode_batch(src, doff)
+    torch.cuda.synchronize()
+    assert np.array_equal(eoff.cpu().numpy(), exp_off)
+    assert np.array_equal(enc.cpu().numpy()[:exp.size], exp)

@@ -1,7 +1,7 @@
 """The kernels of the batched codec against the oracle (exact), on the same
 batches: short messages one thread each with staged per-warp tiles for the
 rest, staged tiles for every message, short messages with unstaged tiles
-(of 8 and of 64 rows), and the flat decode of padded batches (unstaged
+(of 8 and of 64 rows), and the flat kernels of padded batches (unstaged
 tiles for the others), chosen through the shape table's kernel choice (0,
 1, 2, 3), each with buffers on and off a 16-byte boundary. Batches mix empty, tiny and large messages, lengths of
 every class mod 3 and mod 4, messages that straddle tiles and tiles that
@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 URL, NOPAD, STRICT = 1, 2, 4
 # kernel choice, and tile rows of encode and decode
 STAGED, STAGED_ALL, DIRECT, DIRECT_LONG = (0, 16, 8), (1, 16, 8), (2, 8, 8), (2, 64, 64)
-FLAT = (3, 8, 32)  # decode: the flat decode, else unstaged tiles; encode: unstaged tiles
+FLAT = (3, 8, 32)  # the flat kernels where the batch qualifies, else unstaged tiles
 MODES = (STAGED, STAGED_ALL, DIRECT, DIRECT_LONG, FLAT)
 
 
@@ -33,8 +33,7 @@ def kernel_choice(gb64, mode):
     try:
         for k in kinds:
             dec = k == gb64.B64_KIND_DECODE_BATCH
-            gb64.b64_shape_set(k, -1, 1, units_per_thread=kernel if dec else min(kernel, 2),
-                               threads=128, stages=2,
+            gb64.b64_shape_set(k, -1, 1, units_per_thread=kernel, threads=128, stages=2,
                                tile=dec_rows * 512 if dec else enc_rows * 384)
         yield
     finally:

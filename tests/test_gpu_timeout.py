@@ -161,3 +161,21 @@ def test_flat_batch_decode_times_out_then_recovers(gb64, oracle):
     for j in range(0, off.size - 1, 29):
         assert np.array_equal(h[oo[j]:oo[j] + off[j + 1] - off[j]], data[off[j]:off[j + 1]])
     assert gb64.b64_device_fault() == 0
+
+
+def test_flat_batch_encode_times_out_then_recovers(gb64, oracle):
+    """The flat encode of a batch of long messages (the default encode of
+    such batches): CTA 0's first copy is left out and its wait runs out;
+    then the batch encodes exactly."""
+    import torch
+
+    data, off = W.batched(nmsg=3000, seed=46, median=6000.0, sigma=1.0)
+    src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
+    with stalled(gb64):
+        gb64.b64_encode_batch(src, doff)
+        assert gb64.b64_device_fault() == gb64.B64_ERR_TIMEOUT
+    assert gb64.b64_device_fault() == 0
+    benc, boff = gb64.b64_encode_batch(src, doff)
+    oenc, ooff = oracle.encode_batch(data, off)
+    assert np.array_equal(boff.cpu().numpy(), ooff)
+    assert np.array_equal(benc.cpu().numpy()[:oenc.size], oenc)
