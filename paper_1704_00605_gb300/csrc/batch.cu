@@ -1,14 +1,18 @@
 // Batched encode and decode of many packed messages in one kernel per
 // direction.
 //
-//   1. k_scan_local / k_scan_parts / k_scan_add: a device prefix sum over the
+//   1. k_scan_local / k_scan_add: a device prefix sum over the
 //      messages of (output length, weight). Output length is
 //      4 * ceil(n / 3) (encode) or 3 * floor(m / 4) (decode capacity); a
 //      message longer than the short-message limit is cut into
 //      ceil(length / tile) tiles and weighs its length plus a fixed cost per
 //      tile, a shorter one weighs 0. The exclusive sums become out_off
 //      (returned to the caller) and weight_off (scratch).
-//   2. k_batch_code / k_batch_direct (encode or decode): a persistent grid.
+//   2. k_batch_flat / k_batch_flat_enc (kernel choice 3): a batch with
+//      padded encodings of at least 1 Ki characters per message on average
+//      is coded as one buffer (see the flat sections below); the kernels of
+//      step 3 then return at once.
+//   3. k_batch_code / k_batch_direct (encode or decode): a persistent grid.
 //      Its threads first code the short messages one each; then every warp
 //      takes the tiles that start in its equal share of the total weight,
 //      finds the message of its first one by a search in weight_off and
@@ -18,7 +22,8 @@
 //      memory. Both code units with the codecs of common.cuh; per-message
 //      padding (encode) and final quad, error index and length rule
 //      (decode) are handled in the tile that holds the message end.
-//   3. k_batch_decode_finish: per-message status, first_bad and outlen.
+//   4. k_batch_decode_finish: per-message status, first_bad and outlen
+//      (after the flat decode, also each message's final group).
 // All launches have fixed shapes, so a call can be captured in a CUDA graph.
 #include <algorithm>
 
@@ -68,13 +73,14 @@ __device__ __forceinline__ int64_t msg_weight(int64_t len, int64_t tiles) {
   return tiles ? len + tiles * kTileCost : 0;
 }
 
-// Output length and weight of one message.
-__device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, uint32_t flags,
-                                           int64_t small_max, int64_t& outv, int64_t& weight) {
+// Output length and weight of one message (by_tile = DivBy::of(tile)).
+__device__ __forceinline__ void msg_values(int decode, int64_t len, int64_t tile, DivBy by_tile,
+                                           uint32_t flags, int64_t small_max, int64_t& outv,
+                                           int64_t& weight) {
   if (len < 0) len = 0;
   outv = decode ? (int64_t)decoded_cap_flags((uint64_t)len, flags)
                 : (int64_t)encoded_len_flags((uint64_t)len, flags);
-  weight = msg_weight(len, msg_tiles(len, tile, DivBy::of(tile), small_max));
+  weight = msg_weight(len, msg_tiles(len, tile, by_tile, small_max));
 }
 
 // Block-wide exclusive scan of a pair of int64 values; returns the block total.
@@ -128,6 +134,7 @@ __global__ void __launch_bounds__(kScanThreads)
                  int64_t* __restrict__ weight_off, int64_t* __restrict__ part_out,
                  int64_t* __restrict__ part_weight) {
   const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
+  const DivBy by_tile = DivBy::of(tile);
   int64_t vo[kScanItems], vw[kScanItems];
   int64_t so = 0, sw = 0;
 #pragma unroll
@@ -135,7 +142,8 @@ __global__ void __launch_bounds__(kScanThreads)
     const int64_t j = base + i;
     vo[i] = vw[i] = 0;
     if (j < nmsg)
-      msg_values(decode, in_off[j + 1] - in_off[j], tile, flags, small_max, vo[i], vw[i]);
+      msg_values(decode, in_off[j + 1] - in_off[j], tile, by_tile, flags, small_max, vo[i],
+                 vw[i]);
     so += vo[i];
     sw += vw[i];
   }
@@ -157,44 +165,46 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-// One CTA: exclusive scan of the block totals, in place.
-__global__ void __launch_bounds__(kScanThreads)
-    k_scan_parts(int64_t* __restrict__ part_out, int64_t* __restrict__ part_weight,
-                 int64_t nparts) {
-  __shared__ int64_t carry_o, carry_w;
-  if (threadIdx.x == 0) carry_o = carry_w = 0;
-  __syncthreads();
-  for (int64_t c = 0; c < nparts; c += kScanThreads) {
-    const int64_t i = c + threadIdx.x;
-    int64_t a = i < nparts ? part_out[i] : 0, b = i < nparts ? part_weight[i] : 0;
-    int64_t ta, tb;
-    block_exclusive_scan2(a, b, ta, tb);
-    if (i < nparts) {
-      part_out[i] = a + carry_o;
-      part_weight[i] = b + carry_w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      carry_o += ta;
-      carry_w += tb;
-    }
-    __syncthreads();
+// Adds to every message's block-local sums the totals of the scan blocks
+// before its own (summed by the CTA, whose 256 messages share one scan
+// block), and clears the per-message decode results.
+__global__ void __launch_bounds__(256)
+    k_scan_add(int64_t nmsg, int64_t* __restrict__ out_off, int64_t* __restrict__ weight_off,
+               const int64_t* __restrict__ part_out, const int64_t* __restrict__ part_weight,
+               int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
+  static_assert(kScanPerBlock % 256 == 0, "a CTA's messages lie in one scan block");
+  __shared__ int64_t ro[8], rw[8];
+  const int64_t j0 = (int64_t)blockIdx.x * 256;
+  const int64_t p = j0 / kScanPerBlock;
+  int64_t so = 0, sw = 0;
+  for (int64_t i = threadIdx.x; i < p; i += 256) {
+    so += part_out[i];
+    sw += part_weight[i];
   }
-}
-
-__global__ void k_scan_add(int64_t nmsg, int64_t* __restrict__ out_off,
-                           int64_t* __restrict__ weight_off, const int64_t* __restrict__ part_out,
-                           const int64_t* __restrict__ part_weight, int64_t* __restrict__ first_bad,
-                           int64_t* __restrict__ outlen) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    so += __shfl_down_sync(0xFFFFFFFFu, so, d);
+    sw += __shfl_down_sync(0xFFFFFFFFu, sw, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ro[threadIdx.x >> 5] = so;
+    rw[threadIdx.x >> 5] = sw;
+  }
+  __syncthreads();
+  int64_t bo = 0, bw = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    bo += ro[w];
+    bw += rw[w];
+  }
+  const int64_t j = j0 + threadIdx.x;
   if (j == 0) {
     out_off[0] = 0;
     weight_off[0] = 0;
   }
   if (j >= nmsg) return;
-  const int64_t p = j / kScanPerBlock;
-  out_off[j + 1] += part_out[p];
-  weight_off[j + 1] += part_weight[p];
+  out_off[j + 1] += bo;
+  weight_off[j + 1] += bw;
   if (first_bad) first_bad[j] = kNoBad;
   if (outlen) outlen[j] = 0;
 }
@@ -1753,7 +1763,6 @@ cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
     k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
                                                                 small_max, out_off, weight_off,
                                                                 part_out, part_weight);
-    k_scan_parts<<<1, kScanThreads, 0, stream>>>(part_out, part_weight, nparts);
   }
   const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
   k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, weight_off, part_out,
