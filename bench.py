@@ -635,8 +635,9 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_o
         "plain_loop_msgs_per_s": round(2 * k / (plain_loop_ms / 1e3), 1),
         "plain_graph_msgs_per_s": round(2 * k / (plain_graph_ms / 1e3), 1),
         "speedup_vs_plain_graph": round((msgs / batched_ms) / (2 * k / plain_graph_ms), 1),
-        # encode: 3 scan kernels + the tile kernel (short messages first);
-        # decode: the same + the finish kernel
+        # encode: 2 scan kernels, the flat kernel and the tile walk (which
+        # returns at once after a flat batch); decode: the same + the
+        # finish kernel
         "gpu_launches_per_batched_step": BATCHED_LAUNCHES,
     }
 
