@@ -159,12 +159,12 @@ enum {
  * and per-warp tiles staged in shared memory for the longer ones, 1 =
  * staged tiles for every message, 2 = short messages one thread each and
  * unstaged tiles (read and written straight from and to global memory) for
- * the rest, 3 (the default) = a batch whose encoded lengths are all
- * multiples of 4 (padded output; any padded encoding, decoding), of at least
- * 1 Ki characters on average and with src and dst 16-byte aligned, coded as
- * one buffer by a kernel of its own (messages then start on quads of the
- * encoded side, and decoding, every output at 3/4 of its input offset), any
- * other batch as 2. Then threads, tile (input bytes per warp tile, a multiple of
+ * the rest, 3 (the default for decode) = a batch whose encoded lengths are
+ * all multiples of 4 (padded output; any padded encoding, decoding), of at
+ * least 1 Ki characters on average and with src and dst 16-byte aligned,
+ * coded as one buffer by a kernel of its own (messages then start on quads
+ * of the encoded side, and decoding, every output at 3/4 of its input
+ * offset), any other batch as 2. Then threads, tile (input bytes per warp tile, a multiple of
  * 384, or characters, a multiple of 512: up to 16 such rows staged, 64
  * unstaged), stages (staged input stages per warp, 2..6; 0 = 4) and
  * blocks_per_sm (0 = as many as fit); a staged shape's shared memory,

@@ -1569,19 +1569,22 @@ __global__ void __launch_bounds__(kFlatThreads, 1)
     }
     __syncwarp();
     const uint32_t nsg = min(nseg, kFlatMaxSegs);
-    for (uint32_t r = lane; r < (nq + 127u) / 128u; r += 32) {
-      uint32_t lo = 0, hi = nsg;  // the last segment starting at or before quad 128 r
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) / 2;
-        if (segs[mid].x <= (int32_t)(128u * r)) lo = mid; else hi = mid;
+    // the row table by a merge: the lane of segment k fills the rows whose
+    // first quad lies in it (rows past the table's cut keep its last one)
+    const uint32_t nrows = (nq + 127u) / 128u;
+    for (uint32_t k = lane; k < nsg; k += 32) {
+      const int4 g = segs[k];
+      const int32_t q_end = k + 1 < nsg ? segs[k + 1].x : (int32_t)(128u * nrows);
+      const uint32_t r0 = (uint32_t)(max(g.x, 0) + 127) / 128u;
+      const uint32_t r1 = min((uint32_t)(q_end + 127) / 128u, nrows);
+      for (uint32_t r = r0; r < r1; ++r) {
+        const uint32_t qa = 128u * r, qb = qa + 128u;  // the row's quads
+        const bool simple = (int32_t)qb < g.y && qb <= nq &&
+                            ((3u * (qb - 4u) + (uint32_t)g.z) & ~3u) + 16u <= ib &&
+                            (int64_t)3 * qa + g.z >= 0;
+        rowseg[s][r] = (uint16_t)k;
+        rowsd[s][r] = simple ? g.z : kNotSimple;
       }
-      rowseg[s][r] = (uint16_t)lo;
-      const int4 g = segs[lo];
-      const uint32_t qa = 128u * r, qb = qa + 128u;  // the row's quads
-      const bool simple = nsg > 0 && g.x <= (int32_t)qa && (int32_t)qb < g.y && qb <= nq &&
-                          ((3u * (qb - 4u) + (uint32_t)g.z) & ~3u) + 16u <= ib &&
-                          (int64_t)3 * qa + g.z >= 0;
-      rowsd[s][r] = simple ? g.z : kNotSimple;
     }
     __syncwarp();
     if (lane == 0) {

@@ -24,14 +24,16 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
 // average, and 64 of 1 MiB). Decoding longer messages, unstaged tiles of 32
 // rows beat staged ones (a shared-memory output buffer and its bulk store
 // per tile, and tiles limited to 8 rows); encoding, the two are even and
-// staged tiles stay. The flat kernels (kernel 3) take every batch of
-// messages of at least 1 Ki characters on average (padded, and with
-// aligned buffers) and leave the rest to the unstaged tiles. mean_len < 0:
-// unknown.
+// staged tiles stay. Decoding, the flat decode (kernel 3) takes every padded
+// batch of messages of at least 1 Ki characters on average (and aligned
+// buffers) and leaves the rest to the unstaged tiles: 1.2-1.4x faster on
+// every mix measured. The flat encode is left to the shape table: the
+// staged tiles beat it on every mix measured (equal 4 KiB - 1 MiB messages
+// by 1.2-1.3x, the log-normal batch by 2 %). mean_len < 0: unknown.
 BatchConfig default_batch_config(int decode, int64_t mean_len) {
   const bool small = mean_len >= 0 && mean_len < 1024;
   if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 16384, 0, 2, 3};
-  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2, 3};
+  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2};
 }
 
 namespace {

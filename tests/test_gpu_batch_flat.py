@@ -1,4 +1,4 @@
-"""The flat kernels of packed batches (kernel choice 3, the default).
+"""The flat kernels of packed batches (kernel choice 3; the decode default).
 
 Decode: a batch whose encoded lengths are all multiples of 4 decodes as one
 buffer, the last quad of each message (its final group) decoded by the
@@ -10,7 +10,8 @@ unstaged tiles agree; batches that do not qualify (a length not a multiple
 of 4, short messages on average, buffers off a 16-byte boundary) fall back
 to the tile walk and stay exact.
 
-Encode: padded output is one flat sequence of quads; exact against the
+Encode (kernel choice 3 through the shape table; the staged tiles stay the
+default): padded output is one flat sequence of quads; exact against the
 oracle with empty messages, tile-boundary lengths, a tile holding more
 messages than its segment table, the url alphabet, and the fallbacks
 (unpadded output, an unaligned output, short messages)."""
@@ -233,15 +234,11 @@ def test_flat_encode_fallbacks(gb64, oracle):
     assert np.array_equal(_enc_flat(gb64, sdata, soff)[0], oracle.encode_batch(sdata, soff)[0])
 
 
-def test_flat_round_trip_large(gb64, oracle):
-    """The 100,000-message mix encoded and decoded by default (both flat):
-    the encoding equals the oracle's in full, the decode every message."""
-    import torch
-
+def test_flat_encode_large(gb64, oracle):
+    """The 100,000-message mix through the flat encode: the encoding equals
+    the oracle's in full."""
     data, off = W.batched()
     exp, exp_off = oracle.encode_batch(data, off)
-    src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
-    enc, eoff = gb64.b64_encode_batch(src, doff)
-    torch.cuda.synchronize()
-    assert np.array_equal(eoff.cpu().numpy(), exp_off)
-    assert np.array_equal(enc.cpu().numpy()[:exp.size], exp)
+    out, out_off = _enc_flat(gb64, data, off)
+    assert np.array_equal(out_off, exp_off)
+    assert np.array_equal(out, exp)

@@ -164,18 +164,25 @@ def test_flat_batch_decode_times_out_then_recovers(gb64, oracle):
 
 
 def test_flat_batch_encode_times_out_then_recovers(gb64, oracle):
-    """The flat encode of a batch of long messages (the default encode of
-    such batches): CTA 0's first copy is left out and its wait runs out;
-    then the batch encodes exactly."""
+    """The flat encode (kernel choice 3, set through the shape table) of a
+    batch of long messages: CTA 0's first copy is left out and its wait runs
+    out; then the batch encodes exactly."""
     import torch
 
     data, off = W.batched(nmsg=3000, seed=46, median=6000.0, sigma=1.0)
     src, doff = torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda()
-    with stalled(gb64):
-        gb64.b64_encode_batch(src, doff)
-        assert gb64.b64_device_fault() == gb64.B64_ERR_TIMEOUT
-    assert gb64.b64_device_fault() == 0
-    benc, boff = gb64.b64_encode_batch(src, doff)
+    kind = gb64.B64_KIND_ENCODE_BATCH
+    saved = gb64.b64_shape_get(kind, -1, 1)
+    try:
+        gb64.b64_shape_set(kind, -1, 1, threads=256, units_per_thread=3, stages=2, tile=16 * 384)
+        with stalled(gb64):
+            gb64.b64_encode_batch(src, doff)
+            assert gb64.b64_device_fault() == gb64.B64_ERR_TIMEOUT
+        assert gb64.b64_device_fault() == 0
+        benc, boff = gb64.b64_encode_batch(src, doff)
+    finally:
+        gb64.b64_shape_set(kind, -1, 1, **{f: saved[f] for f in (
+            "threads", "units_per_thread", "stages", "blocks_per_sm", "tile")})
     oenc, ooff = oracle.encode_batch(data, off)
     assert np.array_equal(boff.cpu().numpy(), ooff)
     assert np.array_equal(benc.cpu().numpy()[:oenc.size], oenc)
