@@ -635,14 +635,14 @@ def run_batched(args, d: Dist, steps: int = 20, plain_msgs: int = 20_000, nmsg_o
         "plain_loop_msgs_per_s": round(2 * k / (plain_loop_ms / 1e3), 1),
         "plain_graph_msgs_per_s": round(2 * k / (plain_graph_ms / 1e3), 1),
         "speedup_vs_plain_graph": round((msgs / batched_ms) / (2 * k / plain_graph_ms), 1),
-        # encode: 2 scan kernels and the staged tile walk; decode: 2 scan
-        # kernels, the flat decode, the tile walk (which returns at once
+        # encode: the scan kernel and the staged tile walk; decode: the
+        # scan kernel, the flat decode, the tile walk (which returns at once
         # after a flat batch) and the finish kernel
         "gpu_launches_per_batched_step": BATCHED_LAUNCHES,
     }
 
 
-BATCHED_LAUNCHES = 8  # kernels of one batched encode + decode step
+BATCHED_LAUNCHES = 6  # kernels of one batched encode + decode step
 
 
 def batched_line(args, d: Dist):

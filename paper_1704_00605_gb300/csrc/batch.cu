@@ -1,7 +1,7 @@
 // Batched encode and decode of many packed messages in one kernel per
 // direction.
 //
-//   1. k_scan_local / k_scan_add: a device prefix sum over the
+//   1. k_scan_onepass: a device prefix sum (one pass, decoupled look-back) over the
 //      messages of (output length, weight). Output length is
 //      4 * ceil(n / 3) (encode) or 3 * floor(m / 4) (decode capacity); a
 //      message longer than the short-message limit is cut into
@@ -26,6 +26,7 @@
 //      (after the flat decode, also each message's final group).
 // All launches have fixed shapes, so a call can be captured in a CUDA graph.
 #include <algorithm>
+#include <atomic>
 
 #include "batch.h"
 #include "common.cuh"
@@ -128,12 +129,36 @@ __device__ __forceinline__ void block_exclusive_scan2(int64_t& a, int64_t& b, in
   b = pb + ib - b;
 }
 
+// One scan block's totals as the blocks after it see them: flag = the
+// call's number * 4 + kPartAgg (its own totals are published) or kPartInc
+// (its inclusive prefix is published too).
+struct ScanPart {
+  unsigned long long flag;
+  int64_t agg_o, agg_w, inc_o, inc_w;
+};
+constexpr unsigned long long kPartAgg = 1, kPartInc = 2;
+
+// The prefix sum of (output length, weight) in one pass (a decoupled
+// look-back): each CTA scans its 2,048 messages, publishes their totals, and
+// its first warp adds up the totals of the blocks before its own, 32 at a
+// time, walking back until it meets a published inclusive prefix; then
+// every message's offsets are written (and, decoding, first_bad and outlen
+// cleared). The flags carry the call's number (epoch), so the scratch needs
+// no clearing. A block waits only on lower-numbered blocks, which the
+// hardware starts first (and batches of up to about a million messages fit
+// the GPU at once); the waits are bounded by wait_ns all the same, and one
+// that runs out sets the fault word (the calls then report
+// B64_ERR_TIMEOUT) and leaves the offsets unwritten.
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_local(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
-                 uint32_t flags, int64_t small_max, int64_t* __restrict__ out_off,
-                 int64_t* __restrict__ weight_off, int64_t* __restrict__ part_out,
-                 int64_t* __restrict__ part_weight) {
-  const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
+    k_scan_onepass(const int64_t* __restrict__ in_off, int64_t nmsg, int decode, int64_t tile,
+                   uint32_t flags, int64_t small_max, int64_t* __restrict__ out_off,
+                   int64_t* __restrict__ weight_off, volatile ScanPart* parts,
+                   unsigned long long epoch, int64_t* __restrict__ first_bad,
+                   int64_t* __restrict__ outlen, uint64_t wait_ns) {
+  __shared__ int64_t s_base_o, s_base_w;
+  __shared__ uint32_t s_ok;
+  const int64_t blk = blockIdx.x;
+  const int64_t base = blk * kScanPerBlock + (int64_t)threadIdx.x * kScanItems;
   const DivBy by_tile = DivBy::of(tile);
   int64_t vo[kScanItems], vw[kScanItems];
   int64_t so = 0, sw = 0;
@@ -149,64 +174,84 @@ __global__ void __launch_bounds__(kScanThreads)
   }
   int64_t eo = so, ew = sw, to, tw;
   block_exclusive_scan2(eo, ew, to, tw);
+  if (threadIdx.x < 32) {  // warp 0: publish, then look back 32 blocks at a time
+    const uint32_t lane = threadIdx.x;
+    const unsigned long long tagged = epoch << 2;
+    volatile ScanPart* me = parts + blk;
+    if (lane == 0 && blk > 0) {
+      me->agg_o = to;
+      me->agg_w = tw;
+      __threadfence();
+      me->flag = tagged | kPartAgg;
+    }
+    int64_t ex_o = 0, ex_w = 0;
+    bool ok = true;
+    const uint64_t t0 = global_timer_ns();
+    for (int64_t q = blk - 1; q >= 0; q -= 32) {
+      const int64_t mine = q - (int64_t)lane;  // lanes see blocks q, q - 1, .., q - 31
+      const bool valid = mine >= 0;
+      unsigned long long f = 0;
+      for (;;) {  // until every block of the window has published
+        if (valid) f = parts[mine].flag;
+        if (__all_sync(0xFFFFFFFFu, !valid || (f & ~3ull) == tagged)) break;
+        if (__any_sync(0xFFFFFFFFu, global_timer_ns() - t0 > wait_ns)) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+      __threadfence();
+      // the nearest block with its inclusive prefix published ends the walk
+      const uint32_t inc = __ballot_sync(0xFFFFFFFFu, valid && (f & 3ull) == kPartInc);
+      const uint32_t stop = inc ? (uint32_t)(__ffs(inc) - 1) : 32u;
+      int64_t vo = 0, vw = 0;
+      if (valid && lane < stop) {
+        vo = parts[mine].agg_o;
+        vw = parts[mine].agg_w;
+      } else if (valid && lane == stop) {
+        vo = parts[mine].inc_o;
+        vw = parts[mine].inc_w;
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        vo += __shfl_down_sync(0xFFFFFFFFu, vo, d);
+        vw += __shfl_down_sync(0xFFFFFFFFu, vw, d);
+      }
+      ex_o += __shfl_sync(0xFFFFFFFFu, vo, 0);
+      ex_w += __shfl_sync(0xFFFFFFFFu, vw, 0);
+      if (inc) break;
+    }
+    if (lane == 0) {
+      me->inc_o = ex_o + to;
+      me->inc_w = ex_w + tw;
+      __threadfence();
+      me->flag = tagged | kPartInc;
+      s_base_o = ex_o;
+      s_base_w = ex_w;
+      s_ok = ok ? 1u : 0u;
+      if (!ok) atomicOr(&g_batch_fault, 1u);
+    }
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  eo += s_base_o;
+  ew += s_base_w;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t j = base + i;
     eo += vo[i];
     ew += vw[i];
     if (j < nmsg) {
-      out_off[j + 1] = eo;  // inclusive within the block; k_scan_add adds the block base
+      out_off[j + 1] = eo;
       weight_off[j + 1] = ew;
+      if (first_bad) first_bad[j] = kNoBad;
+      if (outlen) outlen[j] = 0;
     }
   }
-  if (threadIdx.x == 0) {
-    part_out[blockIdx.x] = to;
-    part_weight[blockIdx.x] = tw;
-  }
-}
-
-// Adds to every message's block-local sums the totals of the scan blocks
-// before its own (summed by the CTA, whose 256 messages share one scan
-// block), and clears the per-message decode results.
-__global__ void __launch_bounds__(256)
-    k_scan_add(int64_t nmsg, int64_t* __restrict__ out_off, int64_t* __restrict__ weight_off,
-               const int64_t* __restrict__ part_out, const int64_t* __restrict__ part_weight,
-               int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen) {
-  static_assert(kScanPerBlock % 256 == 0, "a CTA's messages lie in one scan block");
-  __shared__ int64_t ro[8], rw[8];
-  const int64_t j0 = (int64_t)blockIdx.x * 256;
-  const int64_t p = j0 / kScanPerBlock;
-  int64_t so = 0, sw = 0;
-  for (int64_t i = threadIdx.x; i < p; i += 256) {
-    so += part_out[i];
-    sw += part_weight[i];
-  }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    so += __shfl_down_sync(0xFFFFFFFFu, so, d);
-    sw += __shfl_down_sync(0xFFFFFFFFu, sw, d);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    ro[threadIdx.x >> 5] = so;
-    rw[threadIdx.x >> 5] = sw;
-  }
-  __syncthreads();
-  int64_t bo = 0, bw = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    bo += ro[w];
-    bw += rw[w];
-  }
-  const int64_t j = j0 + threadIdx.x;
-  if (j == 0) {
+  if (blk == 0 && threadIdx.x == 0) {
     out_off[0] = 0;
     weight_off[0] = 0;
   }
-  if (j >= nmsg) return;
-  out_off[j + 1] += bo;
-  weight_off[j + 1] += bw;
-  if (first_bad) first_bad[j] = kNoBad;
-  if (outlen) outlen[j] = 0;
 }
 
 // ------------------------------------------------------------ tile walk
@@ -1759,17 +1804,13 @@ cudaError_t batch_offsets(int decode, const int64_t* in_off, int64_t nmsg, int64
                           int64_t* weight_off, int64_t tile, void* scratch_parts,
                           int64_t* first_bad, int64_t* outlen, cudaStream_t stream,
                           uint32_t flags, int64_t small_max) {
-  const int64_t nparts = (nmsg + kScanPerBlock - 1) / kScanPerBlock;
-  int64_t* part_out = static_cast<int64_t*>(scratch_parts);
-  int64_t* part_weight = part_out + std::max<int64_t>(nparts, 1);
-  if (nparts > 0) {
-    k_scan_local<<<(unsigned)nparts, kScanThreads, 0, stream>>>(in_off, nmsg, decode, tile, flags,
-                                                                small_max, out_off, weight_off,
-                                                                part_out, part_weight);
-  }
-  const int64_t blocks = std::max<int64_t>(1, (nmsg + 255) / 256);
-  k_scan_add<<<(unsigned)blocks, 256, 0, stream>>>(nmsg, out_off, weight_off, part_out,
-                                                   part_weight, first_bad, outlen);
+  static std::atomic<unsigned long long> calls{0};
+  const unsigned long long epoch = ++calls;  // this call's number (never 0)
+  const int64_t nblocks = std::max<int64_t>(1, (nmsg + kScanPerBlock - 1) / kScanPerBlock);
+  volatile ScanPart* parts = static_cast<volatile ScanPart*>(scratch_parts);
+  k_scan_onepass<<<(unsigned)nblocks, kScanThreads, 0, stream>>>(
+      in_off, nmsg, decode, tile, flags, small_max, out_off, weight_off, parts, epoch, first_bad,
+      outlen, wait_test().limit_ns);
   return cudaGetLastError();
 }
 

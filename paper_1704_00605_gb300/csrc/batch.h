@@ -68,13 +68,14 @@ cudaError_t batch_launch_desc(int decode, const MsgDesc* desc, int64_t nmsg, uin
 constexpr int64_t kBatchScanPerBlock = 512 * 4;
 
 // Bytes of scratch a batch of nmsg messages needs: weight_off (nmsg + 1
-// int64) and the scan's block totals (two int64 per scan block, at least one
-// block).
+// int64) and per scan block its published totals (a flag and four int64; at
+// least one block). Nothing in it needs clearing between calls: the scan
+// tags what it writes with the call's number.
 constexpr size_t batch_scratch_bytes(int64_t nmsg) {
   return (size_t)(nmsg + 1) * 8 +
          (size_t)((nmsg + kBatchScanPerBlock - 1) / kBatchScanPerBlock > 0
                       ? (nmsg + kBatchScanPerBlock - 1) / kBatchScanPerBlock
-                      : 1) * 16;
+                      : 1) * 40;
 }
 
 // Splits a scratch block of batch_scratch_bytes(nmsg) into its arrays.
