@@ -440,17 +440,21 @@ def run_e2e(g, data, d: Dist):
     # quarter of the rate of another's on the same box
     dbuf = torch.empty(GIB, dtype=torch.uint8, device="cuda")
     link = {}
+    # (the best of five single copies: one copy has been seen to run at
+    # under half the rate of the next from the same buffer)
     for name, fn in (("h2d", lambda: dbuf.copy_(h_src[:GIB], non_blocking=True)),
                      ("d2h", lambda: h_dec[:GIB].copy_(dbuf, non_blocking=True)),
                      ("h2d_from_encoded", lambda: dbuf.copy_(h_enc[:GIB], non_blocking=True)),
                      ("d2h_into_encoded", lambda: h_enc[:GIB].copy_(dbuf, non_blocking=True))):
         fn()
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(3):
+        best = float("inf")
+        for _ in range(5):
+            t = time.perf_counter()
             fn()
-        torch.cuda.synchronize()
-        link[name] = round(3 * GIB / (time.perf_counter() - t) / 1e9, 1)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t)
+        link[name] = round(GIB / best / 1e9, 1)
     # both directions at once (two streams): the combined rate of the link
     dbuf2 = torch.empty(GIB, dtype=torch.uint8, device="cuda")
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
@@ -463,11 +467,13 @@ def run_e2e(g, data, d: Dist):
 
     both()
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(3):
+    best = float("inf")
+    for _ in range(5):
+        t = time.perf_counter()
         both()
-    torch.cuda.synchronize()
-    link["both_directions_total"] = round(6 * GIB / (time.perf_counter() - t) / 1e9, 1)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t)
+    link["both_directions_total"] = round(2 * GIB / best / 1e9, 1)
     del dbuf, dbuf2
     k = 6
     d.barrier()
