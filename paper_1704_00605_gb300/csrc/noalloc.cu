@@ -18,8 +18,10 @@
 //   - every call on a device uses the same array, so two calls whose work
 //     overlaps on the GPU (different streams, no ordering) race and give
 //     wrong results: order them on one stream or with events;
-//   - the kernels write every scratch entry they later read within the same
-//     call, so nothing left from the previous call needs clearing;
+//   - nothing left from the previous call needs clearing: the kernels write
+//     every offset and weight entry before reading it in the same call, and
+//     the scan's per-block flags carry each call's number, so a flag left
+//     by an earlier call is never taken for this call's;
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress); make that first call before any stream capture.
 //     The address is kept for the life of the process, so the device must
