@@ -68,6 +68,9 @@ def parse_args(argv=None):
     p.add_argument("--small", action="store_true",
                    help="384 MiB instead of 1 GiB (profiling captures; same launch shapes as "
                         "1 GiB); not a bench value")
+    p.add_argument("--no-plain", action="store_true",
+                   help="with --config batched: the 100,000-message batched calls only, without "
+                        "the one-launch-per-message comparison (profiling captures)")
     p.add_argument("--tiny", action="store_true",
                    help="with --config batched --small: 1,000,000 messages of about 40 bytes "
                         "(one thread each); a profiling case")
@@ -655,6 +658,10 @@ def batched_line(args, d: Dist):
     if args.small and args.tiny:  # 1,000,000 short messages, batched calls only
         b = run_batched(args, d, steps=max(args.steps, 5), plain_msgs=0, nmsg_override=1_000_000,
                         lengths=(40.0, 0.3, 64))
+        return {"metric": "batched msgs/s (profiling case, not a bench value)",
+                "value": b["batched_msgs_per_s"], "unit": "msgs/s", "batched": b}
+    if args.no_plain:  # the 100,000 messages, batched calls only (profiling captures)
+        b = run_batched(args, d, steps=max(args.steps, 5), plain_msgs=0)
         return {"metric": "batched msgs/s (profiling case, not a bench value)",
                 "value": b["batched_msgs_per_s"], "unit": "msgs/s", "batched": b}
     if args.small:  # 20,000 messages, batched calls only (profiling captures)
