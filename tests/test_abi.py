@@ -156,3 +156,17 @@ def test_shape_table_host_side(g, tmp_path):
     g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 40_000, 10, threads=256, tile=2048, blocks_per_sm=8)
     g.b64_tune_load(path)
     assert g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 40_000, 10)["threads"] == 512
+
+
+def test_default_shapes_need_no_gpu(g):
+    """The defaults the shape table answers with when nothing was set or
+    tuned (no GPU needed): batched decode takes the flat decode (kernel
+    choice 3, unstaged 32-row tiles for batches it leaves alone), batched
+    encode the staged 16-row tiles, the whitespace line kernel 512 threads
+    x 7 units x 2 stages for large inputs."""
+    d = g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 123_456_789, 1000)
+    assert (d["units_per_thread"], d["threads"], d["tile"]) == (3, 128, 32 * 512)
+    e = g.b64_shape_get(g.B64_KIND_ENCODE_BATCH, 123_456_789, 1000)
+    assert (e["units_per_thread"], e["threads"], e["tile"], e["stages"]) == (0, 256, 16 * 384, 2)
+    w = g.b64_shape_get(g.B64_KIND_DECODE_WS, 367_332_732, 1)
+    assert (w["threads"], w["units_per_thread"], w["stages"]) == (512, 7, 2)
