@@ -1614,22 +1614,23 @@ __global__ void __launch_bounds__(kFlatThreads, 1)
     }
     __syncwarp();
     const uint32_t nsg = min(nseg, kFlatMaxSegs);
-    // the row table by a merge: the lane of segment k fills the rows whose
-    // first quad lies in it (rows past the table's cut keep its last one)
+    // the row table, one row per lane at a time: the last segment starting
+    // at or before the row's first quad (no search when the tile holds one
+    // message), and the row's shift when it is simple
     const uint32_t nrows = (nq + 127u) / 128u;
-    for (uint32_t k = lane; k < nsg; k += 32) {
-      const int4 g = segs[k];
-      const int32_t q_end = k + 1 < nsg ? segs[k + 1].x : (int32_t)(128u * nrows);
-      const uint32_t r0 = (uint32_t)(max(g.x, 0) + 127) / 128u;
-      const uint32_t r1 = min((uint32_t)(q_end + 127) / 128u, nrows);
-      for (uint32_t r = r0; r < r1; ++r) {
-        const uint32_t qa = 128u * r, qb = qa + 128u;  // the row's quads
-        const bool simple = (int32_t)qb < g.y && qb <= nq &&
-                            ((3u * (qb - 4u) + (uint32_t)g.z) & ~3u) + 16u <= ib &&
-                            (int64_t)3 * qa + g.z >= 0;
-        rowseg[s][r] = (uint16_t)k;
-        rowsd[s][r] = simple ? g.z : kNotSimple;
+    for (uint32_t r = lane; r < nrows; r += 32) {
+      const uint32_t qa = 128u * r, qb = qa + 128u;  // the row's quads
+      uint32_t lo = 0, hi = nsg;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (segs[mid].x <= (int32_t)qa) lo = mid; else hi = mid;
       }
+      const int4 g = segs[lo];
+      const bool simple = nsg > 0 && (int32_t)qb < g.y && qb <= nq &&
+                          ((3u * (qb - 4u) + (uint32_t)g.z) & ~3u) + 16u <= ib &&
+                          (int64_t)3 * qa + g.z >= 0;
+      rowseg[s][r] = (uint16_t)lo;
+      rowsd[s][r] = simple ? g.z : kNotSimple;
     }
     __syncwarp();
     if (lane == 0) {
