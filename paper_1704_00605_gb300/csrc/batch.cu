@@ -450,6 +450,43 @@ __device__ __forceinline__ void copy_out(uint8_t* d, uint32_t olen, const uint8_
   }
 }
 
+// The batched encoders code each 12-bit half of a group with one lookup in
+// a table of character pairs: entry v holds the characters of the 6-bit
+// values v >> 6 (low byte) and v & 63 (high byte). The pairs follow the
+// 64-character alphabet in each encoding kernel's table (kEncTableBytes in
+// all), so a coder handed the alphabet T finds them at T + 64. Two 16-bit
+// lookups and two field extractions per group take the place of four byte
+// lookups and four extractions.
+constexpr uint32_t kEncTableBytes = 64u + 2u * 4096u;
+
+__device__ __forceinline__ void init_enc_pairs(uint8_t* T, bool url) {
+  uint16_t* P = reinterpret_cast<uint16_t*>(T + 64);
+  for (uint32_t v = threadIdx.x; v < 4096u; v += blockDim.x)
+    P[v] = (uint16_t)(alphabet_char(v >> 6, url) | (alphabet_char(v & 63u, url) << 8));
+  for (uint32_t v = threadIdx.x; v < 64u; v += blockDim.x) T[v] = (uint8_t)alphabet_char(v, url);
+  __syncthreads();
+}
+
+// One group (three bytes big-endian in bits 23..0; bits above 23 are
+// ignored) -> four characters, first in the low byte.
+__device__ __forceinline__ uint32_t enc_group_pairs(uint32_t g, const uint8_t* T) {
+  const uint8_t* P = T + 64;
+  const uint32_t a = *reinterpret_cast<const uint16_t*>(P + ((g >> 11) & 0x1FFEu));
+  const uint32_t b = *reinterpret_cast<const uint16_t*>(P + ((g << 1) & 0x1FFEu));
+  return __byte_perm(a, b, 0x5410);
+}
+
+// Stream bytes x0..x11 in little-endian words w0, w1, w2 -> 16 characters.
+__device__ __forceinline__ uint4 enc_unit_pairs(uint32_t w0, uint32_t w1, uint32_t w2,
+                                                const uint8_t* T) {
+  uint4 o;
+  o.x = enc_group_pairs(__byte_perm(w0, 0u, 0x4012), T);  // x0 x1 x2
+  o.y = enc_group_pairs(__byte_perm(w0, w1, 0x3345), T);  // x3 x4 x5
+  o.z = enc_group_pairs(__byte_perm(w1, w2, 0x2234), T);  // x6 x7 x8
+  o.w = enc_group_pairs(__byte_perm(w2, 0u, 0x4123), T);  // x9 x10 x11
+  return o;
+}
+
 // Input words of the 12 tile bytes at off: from the stage when they were
 // all copied there, else from global memory (off + 12 <= the tile's length).
 __device__ __forceinline__ uint3 enc_load(const TileView& v, const uint8_t* in, const uint8_t* sp,
@@ -486,7 +523,7 @@ __device__ __forceinline__ void enc_chunks(const uint8_t* sb, uint8_t* db, int32
       y = __funnelshift_r(q1, q2, 8 * R);
       z = __funnelshift_r(q2, q3, 8 * R);
     }
-    st_global_v4_cs(db + 16 * i, enc_unit(x, y, z, T));
+    st_global_v4_cs(db + 16 * i, enc_unit_pairs(x, y, z, T));
   }
 }
 
@@ -519,7 +556,7 @@ __device__ __forceinline__ void enc_chunks_global(const uint8_t* s, uint8_t* db,
         const uint32_t x = R ? __funnelshift_r(q[k][0], q[k][1], 8 * R) : q[k][0];
         const uint32_t y = R ? __funnelshift_r(q[k][1], q[k][2], 8 * R) : q[k][1];
         const uint32_t z = R ? __funnelshift_r(q[k][2], q[k][3], 8 * R) : q[k][2];
-        st_global_v4_cs(db + 16 * i, enc_unit(x, y, z, T));
+        st_global_v4_cs(db + 16 * i, enc_unit_pairs(x, y, z, T));
       }
     }
   }
@@ -610,7 +647,7 @@ __device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in
       const bool head = q && c == 0, tail = q && c == n;
       const uint32_t off = head ? 0u : (tail ? 12u * (nu - 1u) : 12u * (uint32_t)c - 3u * q);
       const uint3 w = enc_load(v, in, sp, off);
-      const uint4 e = enc_unit(w.x, w.y, w.z, T);
+      const uint4 e = enc_unit_pairs(w.x, w.y, w.z, T);
       if (!head && !tail) {
         st_global_v4_cs(abase + 16u * (uint32_t)c, e);
       } else {
@@ -626,7 +663,7 @@ __device__ __forceinline__ void encode_tile(const TileView& v, const uint8_t* in
       uint4 c = make_uint4(0u, 0u, 0u, 0u);
       if (u < nu) {
         const uint3 w = enc_load(v, in, sp, 12u * u);
-        c = enc_unit(w.x, w.y, w.z, T);
+        c = enc_unit_pairs(w.x, w.y, w.z, T);
       }
       uint4 prev;
       prev.x = __shfl_up_sync(0xFFFFFFFFu, c.x, 1);
@@ -831,7 +868,7 @@ __device__ __forceinline__ void encode_message(const uint8_t* p, int64_t n, uint
       if (u0 + k < nu) w[k] = load12_any(p + 12 * (u0 + k), lo, hi);
 #pragma unroll
     for (uint32_t k = 0; k < 4; ++k)
-      if (u0 + k < nu) store16_any(d + 16 * (u0 + k), enc_unit(w[k].x, w[k].y, w[k].z, T));
+      if (u0 + k < nu) store16_any(d + 16 * (u0 + k), enc_unit_pairs(w[k].x, w[k].y, w[k].z, T));
   }
   const uint32_t rest = (uint32_t)n - 12 * nu;
   for (uint32_t g = 0; 3 * g < rest; ++g) {  // whole groups, then the partial one
@@ -986,7 +1023,7 @@ __global__ void __launch_bounds__(NT)
                  uint32_t stages, int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen,
                  uint32_t flags, WaitTest wt) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint8_t table[DECODE ? 256 : 64];
+  __shared__ __align__(16) uint8_t table[DECODE ? 256 : kEncTableBytes];
   __shared__ __align__(8) uint64_t full[NT / 32][kMaxBatchStages];
   __shared__ TileView meta[NT / 32][kMaxBatchStages];
   __shared__ WalkState walks[NT / 32];
@@ -999,7 +1036,7 @@ __global__ void __launch_bounds__(NT)
   if (DECODE) {
     init_tables(nullptr, table, flags & kFlagUrl);
   } else {
-    init_tables(table, nullptr, flags & kFlagUrl);
+    init_enc_pairs(table, flags & kFlagUrl);
   }
   const uint32_t in_b = stage_in_bytes(ts.tile);
   uint8_t* wbase = smem + (size_t)warp * warp_smem_bytes(DECODE, ts.tile, S);
@@ -1098,13 +1135,13 @@ __global__ void __launch_bounds__(NT)
     k_batch_direct(Msgs msgs, int64_t nmsg, const int64_t* __restrict__ weight_off, TileShape ts,
                    int64_t* __restrict__ first_bad, int64_t* __restrict__ outlen, uint32_t flags,
                    uint32_t after_flat) {
-  __shared__ uint8_t table[DECODE ? 256 : 64];
+  __shared__ __align__(16) uint8_t table[DECODE ? 256 : kEncTableBytes];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (after_flat && (DECODE ? flat_batch(msgs, nmsg) : flat_enc_batch(msgs, nmsg))) return;
   if (DECODE) {
     init_tables(nullptr, table, flags & kFlagUrl);
   } else {
-    init_tables(table, nullptr, flags & kFlagUrl);
+    init_enc_pairs(table, flags & kFlagUrl);
   }
   int64_t w_begin, w_end;
   warp_share(weight_off, nmsg, (int64_t)blockIdx.x * (NT / 32) + warp,

@@ -99,9 +99,12 @@ int64_t batch_small_max(int decode);
 cudaError_t batch_launch(const BatchArgs& a, const BatchConfig& cfg);
 
 // Largest dynamic shared memory a valid batch shape may ask for: the
-// opt-in limit of a CTA on sm_103 (227 KiB) less the kernel's static tables,
-// barriers and tile views. A launch still checks the device it runs on.
-constexpr size_t kBatchSmemLimit = 227 * 1024 - 8 * 1024;
+// opt-in limit of a CTA on sm_103 (227 KiB) less the kernel's static shared
+// memory (tables, barriers and tile views): up to 9.5 KiB decoding, and up
+// to 17.4 KiB encoding, whose table holds 8 KiB of character pairs (512
+// threads). A launch still checks the device it runs on.
+constexpr size_t kBatchSmemLimitDecode = 227 * 1024 - 10 * 1024;
+constexpr size_t kBatchSmemLimitEncode = 227 * 1024 - 18 * 1024;
 
 // Dynamic shared memory of a batched launch: per warp, `stages` input
 // stages of a tile (and, decoding, one output buffer).

@@ -16,7 +16,7 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
   const int64_t row = decode ? 512 : 384;  // one unit per lane of a warp
   const int64_t max_rows = c.kernel >= 2 ? 64 : 16;  // unstaged tiles need no shared memory
   if (c.tile < row || c.tile > max_rows * row || c.tile % row) return false;
-  return batch_smem_bytes(decode, c) <= kBatchSmemLimit;
+  return batch_smem_bytes(decode, c) <= (decode ? kBatchSmemLimitDecode : kBatchSmemLimitEncode);
 }
 
 // Shapes measured fastest on GB300: mean message length below 1 KiB
@@ -29,11 +29,13 @@ bool batch_config_valid(int decode, const BatchConfig& c) {
 // buffers) and leaves the rest to the unstaged tiles: 1.2-1.4x faster on
 // every mix measured. The flat encode is left to the shape table: the
 // staged tiles beat it on every mix measured (equal 4 KiB - 1 MiB messages
-// by 1.2-1.3x, the log-normal batch by 2 %). mean_len < 0: unknown.
+// by 1.2-1.3x, the log-normal batch by 1.1x); one CTA of 16 warps per SM
+// beats two of 8 by 2 % on the log-normal batch and ties elsewhere.
+// mean_len < 0: unknown.
 BatchConfig default_batch_config(int decode, int64_t mean_len) {
   const bool small = mean_len >= 0 && mean_len < 1024;
   if (decode) return small ? BatchConfig{128, 1024, 0, 2} : BatchConfig{128, 16384, 0, 2, 3};
-  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{256, 6144, 0, 2};
+  return small ? BatchConfig{256, 1536, 0, 2} : BatchConfig{512, 6144, 0, 2};
 }
 
 namespace {

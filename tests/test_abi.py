@@ -133,6 +133,10 @@ def test_shape_table_host_side(g, tmp_path):
         g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=512, tile=8192, stages=4)
     with pytest.raises(g.Gb64Error):
         g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=128, tile=1536, stages=7)
+    with pytest.raises(g.Gb64Error):  # 16 warps x 3 stages x 4.5 KiB: no room left for the
+        # encode kernel's static tables (17.4 KiB with the 8 KiB pair table) under 227 KiB
+        g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=512, tile=12 * 384, stages=3)
+    g.b64_shape_set(g.B64_KIND_ENCODE_BATCH, 10_000, 10, threads=512, tile=16 * 384, stages=2)
     # unstaged tiles (kernel choice 2) use no shared memory: up to 64 rows
     g.b64_shape_set(g.B64_KIND_DECODE_BATCH, 10_000, 10, threads=512, tile=64 * 512, stages=2,
                     units_per_thread=2)
@@ -162,11 +166,11 @@ def test_default_shapes_need_no_gpu(g):
     """The defaults the shape table answers with when nothing was set or
     tuned (no GPU needed): batched decode takes the flat decode (kernel
     choice 3, unstaged 32-row tiles for batches it leaves alone), batched
-    encode the staged 16-row tiles, the whitespace line kernel 512 threads
+    encode the staged 16-row tiles (16 warps), the whitespace line kernel 512 threads
     x 7 units x 2 stages for large inputs."""
     d = g.b64_shape_get(g.B64_KIND_DECODE_BATCH, 123_456_789, 1000)
     assert (d["units_per_thread"], d["threads"], d["tile"]) == (3, 128, 32 * 512)
     e = g.b64_shape_get(g.B64_KIND_ENCODE_BATCH, 123_456_789, 1000)
-    assert (e["units_per_thread"], e["threads"], e["tile"], e["stages"]) == (0, 256, 16 * 384, 2)
+    assert (e["units_per_thread"], e["threads"], e["tile"], e["stages"]) == (0, 512, 16 * 384, 2)
     w = g.b64_shape_get(g.B64_KIND_DECODE_WS, 367_332_732, 1)
     assert (w["threads"], w["units_per_thread"], w["stages"]) == (512, 7, 2)
