@@ -456,7 +456,9 @@ __device__ __forceinline__ void copy_out(uint8_t* d, uint32_t olen, const uint8_
 // 64-character alphabet in each encoding kernel's table (kEncTableBytes in
 // all), so a coder handed the alphabet T finds them at T + 64. Two 16-bit
 // lookups and two field extractions per group take the place of four byte
-// lookups and four extractions.
+// lookups and four extractions: Algorithm 1's map B applied to two values
+// at once, the trade of a larger table for fewer shifts and masks that
+// Section 2.2 describes for scalar encoders.
 constexpr uint32_t kEncTableBytes = 64u + 2u * 4096u;
 
 __device__ __forceinline__ void init_enc_pairs(uint8_t* T, bool url) {
